@@ -1,0 +1,423 @@
+"""Benchmark: amplitude-steps/s of a reversible wiring diagram on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload mixed_m28|adder_m32|cnot_m16]
+
+One timed step = one pass of the whole hot path over the resident state:
+validate + plan the circuit, apply all of its steps (qsim_apply_circuit) and
+compute the FP64 basis-state probabilities into device memory
+(qsim_probabilities_device).  value = 2^M * L * K / (device time of K steps).
+
+Default workload: M=28 complex128 (4 GiB state, larger than L2), L=1000 steps
+of the NOT / CNOT / Toffoli / 3-5-control NOT mix, seeded synthetic state and
+circuit.  Adjacent-equal-step cancellation is switched off, so every one of
+the L steps is applied.
+
+Also reported on the same JSON line:
+  e2e          the same metric through the C ABI with host buffers: each step
+               copies the state in from pinned host memory, applies the
+               circuit, computes probabilities and copies them back.
+  roofline     the dominant kernel's algorithmic bytes per launch over its
+               average CUDA-event duration, against the measured HBM copy
+               bandwidth (MEASURED_PEAKS.json).
+  cpu_baseline the CPU oracle on the host cores, on a bounded prefix of the
+               same circuit and state.
+  clocks       nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the CPU oracle alone (the reference arm).
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload; value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_quant_ph_0308158_gb300 import workloads as W  # noqa: E402
+
+METRIC = "amplitude-steps/s"
+UNIT = "amp-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCE = os.path.join(ROOT, "paper_quant_ph_0308158_gb300", "csrc", "kernels.cu")
+
+
+def workload(name: str):
+    if name == "mixed_m28":
+        return W.config_mixed_m28()
+    if name == "adder_m32":
+        return W.config_adder_m32()
+    if name == "cnot_m16":
+        return W.config_small_cnot()
+    raise SystemExit("unknown workload " + name)
+
+
+def strategy_for(name: str) -> str:
+    # the adder workload is specified in place
+    return "inplace" if name == "adder_m32" else "auto"
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only; no data-path collective)
+# ----------------------------------------------------------------------------
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# roofline inputs
+# ----------------------------------------------------------------------------
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(KERNEL_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel_kind: str, wl: str):
+    """DRAM bytes per launch recorded from an ncu capture of the current kernel
+    source (profiles/traffic.json), scaled to the benchmarked launch; None if
+    absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get(wl, {}).get(kernel_kind)
+    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle
+# ----------------------------------------------------------------------------
+
+def oracle_sample_rate(cfg, n_steps: int, k1=None):
+    """Time the CPU oracle applying the first n_steps of the circuit to the full
+    state (single thread).  Returns (amp-steps/s, seconds)."""
+    import oracle
+    oracle.build()
+    M = cfg["M"]
+    if k1 is None:
+        k1 = W.random_state(M, cfg["dtype"], cfg["state_seed"])
+    steps = cfg["steps"][:n_steps]
+    t0 = time.perf_counter()
+    oracle.apply_circuit(M, k1, steps)
+    dt = time.perf_counter() - t0
+    return (1 << M) * n_steps / dt, dt
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    cfg = workload(args.workload)
+    M = cfg["M"]
+    k1 = W.random_state(M, cfg["dtype"], cfg["state_seed"])
+    per = max(1, min(len(cfg["steps"]), args.ref_steps_per_step))
+    for _ in range(args.warmup):
+        oracle_sample_rate(cfg, per, k1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample_rate(cfg, per, k1)
+        times.append(dt)
+    total = sum(times)
+    value = (1 << M) * per * args.steps / total
+    sample = "first %d of the %d circuit steps on the full 2^%d-amplitude state, per timed step" % (
+        per, len(cfg["steps"]), M)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if np.dtype(cfg["dtype"]) == np.complex128 else "c64",
+        "data": "synthetic", "config": {"workload": cfg["name"], "M": M, "L": len(cfg["steps"])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_quant_ph_0308158_gb300 import Simulator, build
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    build.build()
+    torch.cuda.set_device(local)
+    cfg = workload(args.workload)
+    M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
+    L = len(steps)
+    n = 1 << M
+    amp = dtype.itemsize
+    strategy = strategy_for(args.workload)
+    tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
+
+    # seeded state in pinned host memory (also the e2e input buffer)
+    h_in_t = torch.empty(n, dtype=tdt, pin_memory=True)
+    h_in = h_in_t.numpy()
+    W.random_state(M, dtype, cfg["state_seed"], out=h_in)
+
+    sim = Simulator(M, dtype, scratch=(strategy != "inplace"))
+    sim.set_strategy(strategy)
+    sim.set_canonicalize(False)
+    probs = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sim.apply(steps)
+        sim.probabilities_device(probs.data_ptr())
+
+    # ---- device-resident timing ------------------------------------------------
+    sim.load_state(h_in)
+    for _ in range(args.warmup):
+        step()
+    sim.synchronize()
+    sim.set_profiling(True)
+    sim.pass_times()  # clear
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    passes = sim.pass_times()
+    sim.set_profiling(False)
+    stats = sim.plan_stats()
+    ms_total = max_over_ranks(ms_total, ws)
+    ms_step = ms_total / args.steps
+    value = ws * n * L * args.steps / (ms_total * 1e-3)
+
+    # dominant kernel (most device time in the timed region)
+    by_kind = {}
+    for kind, ms, by in passes:
+        a = by_kind.setdefault(kind, [0, 0.0, 0.0])
+        a[0] += 1
+        a[1] += ms
+        a[2] += by
+    dom = max(by_kind.items(), key=lambda kv: kv[1][1])
+    dkind, (dlaunch, dms, dbytes) = dom
+    peak, peak_src = hbm_peak()
+    achieved = (dbytes / dlaunch) / (dms / dlaunch * 1e-3) / 1e9
+    traffic = ncu_traffic(dkind, cfg["name"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": {"gather": "gather_sliced_kernel" if L > 0 else "gather",
+                           "tile": "tile_kernel", "sweep": "sweep_kernel"}[dkind],
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6800 GB/s",
+                "algorithmic_bytes_per_launch": dbytes / dlaunch,
+                "avg_launch_ms": dms / dlaunch, "launches": dlaunch}
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        h_out_t = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_out = h_out_t.numpy()
+        h2d = n * amp
+        d2h = n * 8
+
+        def e2e_step():
+            sim.load_state(h_in)
+            sim.apply(steps)
+            sim.probabilities(out=h_out)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        ke = max(1, args.steps)
+        f0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws)
+        e2e = {"value": ws * n * L * ke / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": ms_e2e / ke}
+        del h_out
+
+    # ---- CPU baseline: the oracle on a bounded prefix (rank 0, N=1) -----------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        nst = min(L, args.cpu_steps)
+        rate, secs = oracle_sample_rate(cfg, nst, h_in)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d of the %d steps on the full 2^%d-amplitude state (%.1f s)" % (
+                   nst, L, M, secs)}
+
+    launches = len(passes) + args.steps * 2  # passes + (probabilities + norm reduce) per step
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if dtype == np.complex128 else "c64",
+            "data": "synthetic (seeded random state and circuit)",
+            "config": {"workload": cfg["name"], "M": M, "L": L, "strategy": strategy,
+                       "state_bytes": n * amp, "l2": "inputs larger than L2",
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "passes_per_step": stats["passes"],
+                       "gather_passes": stats["gather_passes"],
+                       "tile_passes": stats["tile_passes"],
+                       "sweep_passes": stats["sweep_passes"],
+                       "steps_cancelled": stats["steps_cancelled"],
+                       "full_pass_equiv": stats["full_pass_equiv"],
+                       "step_includes": "plan + all passes + FP64 probabilities"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "cnot_m16"])
+    ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
+    ap.add_argument("--ref-steps-per-step", type=int, default=2,
+                    help="oracle steps per timed reference step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: timing rules want >= 3 warm-up steps", file=sys.stderr)
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        rc = run_reference(args, rank, ws)
+    else:
+        rc = run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector engine for reversible wiring
+ * diagrams (J. R. Burger, "New approaches to quantum computer simulation in
+ * a classical supercomputer").
+ *
+ * The engine applies a wiring diagram of L steps -- NOT, controlled-NOT,
+ * Toffoli and multi-controlled NOT -- to a state vector of 2^M complex
+ * amplitudes held in GPU memory.  Each step is a symmetric permutation
+ * matrix with one unit entry per row (Sec. 2a), so the engine only moves
+ * amplitudes: states come back bit-exact.
+ *
+ * Index convention (Sec. 2b): bit b of a state index is the paper's address
+ * wire a(b+1); a(1) is the least significant bit.  A step's target bit is
+ * the paper's 'goto' wire minus one; its control bits are the 'from' wires.
+ *
+ * Memory layout: amplitude i sits at byte offset i * sizeof(amplitude),
+ * interleaved (re, im): two floats for QSIM_C64, two doubles for
+ * QSIM_C128.  Host buffers passed in are owned by the caller and only read
+ * or written during the call.  Device buffers are owned by the library
+ * unless created with qsim_create_with_buffers.
+ *
+ * Errors: every int-returning call returns QSIM_OK (0) or a negative code;
+ * qsim_last_error() then describes the failure (thread-local string).  A
+ * call that fails validation changes nothing.  Calls on one context must
+ * not overlap from different host threads.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QSIM_OK 0
+#define QSIM_EINVAL (-1)   /* bad argument: M, dtype, step, size or pointer */
+#define QSIM_ENOMEM (-2)   /* a device or host allocation failed          */
+#define QSIM_ECUDA (-3)    /* a CUDA runtime call failed                   */
+#define QSIM_ETIMEOUT (-4) /* a bounded device-side wait gave up           */
+#define QSIM_EBUSY (-5)    /* admission refused: over the memory budget    */
+#define QSIM_ENOTFOUND (-6)/* unknown request id                           */
+
+#define QSIM_MAX_QUBITS 34 /* 2^34 amplitudes: 128 GiB (c64), 256 GiB (c128) */
+
+typedef enum { QSIM_C64 = 0, QSIM_C128 = 1 } qsim_dtype;
+
+/* One wiring-diagram step (Sec. 2b-2g).  The amplitude pair (i, i ^ 2^target)
+ * is exchanged for every index i with (i & ctrl_mask) == ctrl_pol:
+ *   ctrl_mask == 0          NOT on a(target+1)                (Sec. 2e)
+ *   one bit in ctrl_mask    controlled-NOT, 'from' above or below 'goto'
+ *                           (Sec. 2b, 2c, 2f)
+ *   two bits                Toffoli (Sec. 2g)
+ *   more bits               multi-controlled NOT (Sec. 2g)
+ * ctrl_pol bit = 1 fires on |1> of that control, 0 on |0>.  Valid steps:
+ * target < M, target not in ctrl_mask, ctrl_mask < 2^M, ctrl_pol a subset
+ * of ctrl_mask, reserved == 0.  24 bytes, no padding. */
+typedef struct qsim_step {
+    uint32_t target;
+    uint32_t reserved;
+    uint64_t ctrl_mask;
+    uint64_t ctrl_pol;
+} qsim_step;
+
+/* Kernel strategies.  AUTO lets the planner choose per segment. */
+typedef enum {
+    QSIM_STRATEGY_AUTO = 0,
+    QSIM_STRATEGY_SWEEP = 1,  /* one in-place pass per step over the toggled
+                                 pairs only (Sec. 2b 'intelligent looping') */
+    QSIM_STRATEGY_TILE = 2,   /* in-place passes, each applying a run of steps
+                                 whose targets lie in one tile of address bits
+                                 (Sec. 2i: sequential steps processed together) */
+    QSIM_STRATEGY_GATHER = 3, /* out-of-place passes k2(i) = k1(x(i)) with x
+                                 evaluated per index (Sec. 2h product, final
+                                 gather); needs a scratch buffer */
+    QSIM_STRATEGY_INPLACE = 4 /* AUTO restricted to in-place passes: the state
+                                 never leaves its buffer, no scratch is used */
+} qsim_strategy;
+
+typedef struct qsim_ctx qsim_ctx;
+
+/* Statistics of the most recent qsim_apply_circuit on a context. */
+typedef struct qsim_plan_stats {
+    uint64_t steps_in;        /* steps passed in                                 */
+    uint64_t steps_cancelled; /* adjacent equal steps removed (each is an involution) */
+    uint64_t passes;          /* kernel launches over the state                  */
+    uint64_t sweep_passes;    /* of which pair-swap sweeps                       */
+    uint64_t tile_passes;     /* of which tile passes                            */
+    uint64_t gather_passes;   /* of which index-gather passes                    */
+    double algorithmic_bytes; /* sum over passes of bytes read + written as the
+                                 method requires (untouched tiles/pairs excluded) */
+    double full_pass_equiv;   /* algorithmic_bytes / (2 * state bytes)           */
+} qsim_plan_stats;
+
+/* ---- context lifetime --------------------------------------------------- */
+
+/* Create a context for a 2^M-amplitude state of the given dtype on the
+ * current CUDA device, allocate its state (cudaMalloc, zero-filled; no scratch
+ * until a gather pass needs one) and a private stream.  M in [1, QSIM_MAX_QUBITS].
+ * Returns QSIM_EINVAL for bad M/dtype, QSIM_ENOMEM when the state does not fit. */
+int qsim_create(uint32_t M, int dtype, qsim_ctx **out);
+
+/* Create a context over caller-owned device memory (e.g. tensors from the
+ * PyTorch caching allocator).  d_state: 2^M amplitudes, 256-byte aligned.
+ * d_scratch: NULL or a second buffer of the same size, enabling gather
+ * passes.  stream: a cudaStream_t (NULL = legacy default stream) on which
+ * every kernel of the context runs.  The caller keeps ownership and must
+ * keep the buffers alive until qsim_destroy.  After qsim_apply_circuit the
+ * current state may sit in either buffer: ask qsim_state_device(). */
+int qsim_create_with_buffers(uint32_t M, int dtype, void *d_state, void *d_scratch,
+                             void *stream, qsim_ctx **out);
+
+/* Release the context and every device buffer it owns.  NULL is ignored. */
+void qsim_destroy(qsim_ctx *ctx);
+
+/* ---- state transfer (the paper's k1 in, k2 out) -------------------------- */
+
+/* Copy 2^M amplitudes from host memory into the state (k1, Sec. 2b).
+ * n_amps must equal 2^M.  Synchronous with respect to host_amps. */
+int qsim_load_state(qsim_ctx *ctx, const void *host_amps, size_t n_amps);
+
+/* Copy the state (k2) to host memory; n_amps must equal 2^M.  Waits for all
+ * work queued on the context and reports device-side errors. */
+int qsim_read_state(qsim_ctx *ctx, void *host_amps, size_t n_amps);
+
+/* Device pointer of the buffer that holds the current state. */
+void *qsim_state_device(qsim_ctx *ctx);
+
+/* ---- the wiring diagram ---------------------------------------------------- */
+
+/* Apply steps[0], steps[1], ..., steps[L-1] in that order:
+ * k2 = U_L ... U_1 k1 (Sec. 2a, 2h; Summary of Method).  All steps are
+ * validated first; on QSIM_EINVAL nothing is applied.  The steps are copied
+ * during the call.  Work is queued on the context's stream and the call
+ * returns without waiting for it; errors of queued kernels surface at the
+ * next qsim_synchronize / qsim_read_state / qsim_probabilities. */
+int qsim_apply_circuit(qsim_ctx *ctx, const qsim_step *steps, size_t L);
+
+/* Force a strategy for subsequent qsim_apply_circuit calls (tests and
+ * tuning).  tile_bits: total tile width k (0 = default), low_bits: how many
+ * of them are the lowest address bits (0 = default). */
+int qsim_set_strategy(qsim_ctx *ctx, int strategy, int tile_bits, int low_bits);
+
+/* Adjacent equal steps cancel in pairs (each step is its own inverse,
+ * Sec. 2a).  enable = 1 (default) removes them before planning; 0 applies
+ * every step as given. */
+int qsim_set_canonicalize(qsim_ctx *ctx, int enable);
+
+/* Statistics of the last qsim_apply_circuit. */
+int qsim_get_plan_stats(qsim_ctx *ctx, qsim_plan_stats *out);
+
+/* Per-pass device timing (tracing).  With enable = 1, every pass launched by
+ * qsim_apply_circuit is bracketed by CUDA events on the context's stream, and
+ * the records accumulate over successive applies.  qsim_get_pass_times waits
+ * for queued work and writes, for each recorded pass (at most cap), the
+ * device time in milliseconds, the pass kind (1 sweep, 2 tile, 3 gather) and
+ * its algorithmic bytes (any pointer may be NULL); *n_out receives the number
+ * of recorded passes.  When cap covers them all the record is cleared. */
+int qsim_set_profiling(qsim_ctx *ctx, int enable);
+int qsim_get_pass_times(qsim_ctx *ctx, double *ms, uint32_t *kinds, double *alg_bytes,
+                        size_t cap, size_t *n_out);
+
+/* Wait for queued work; returns QSIM_ETIMEOUT / QSIM_ECUDA if a kernel failed. */
+int qsim_synchronize(qsim_ctx *ctx);
+
+/* ---- post-processing ----------------------------------------------------- */
+
+/* FP64 basis-state probabilities p(i) = re^2 + im^2 (products rounded
+ * separately, no fused multiply-add) into host_probs[0 .. 2^M-1]; n must be
+ * 2^M.  norm_out (may be NULL) receives sum_i p(i), reduced in FP64 on the
+ * device.  Synchronous. */
+int qsim_probabilities(qsim_ctx *ctx, double *host_probs, size_t n, double *norm_out);
+
+/* As qsim_probabilities, into device memory d_probs (2^M doubles, 8-byte
+ * aligned), queued on the context's stream.  norm_out (may be NULL) is a
+ * host pointer; when given the call waits for the result. */
+int qsim_probabilities_device(qsim_ctx *ctx, double *d_probs, double *norm_out);
+
+/* ---- host-only planning (no GPU needed) ------------------------------------ */
+
+/* Plan a circuit exactly as qsim_apply_circuit would, without touching a GPU
+ * (the segmentation of Sec. 2i into passes).  Inputs as for
+ * qsim_set_strategy plus scratch_available (nonzero: gather passes allowed).
+ * Outputs, each optional (NULL skips it):
+ *   stats      -- as qsim_get_plan_stats
+ *   order      -- circuit index of every applied step, in application order
+ *                 (length = steps_in - steps_cancelled, at most cap)
+ *   pass_ends  -- exclusive end in 'order' of each pass (length = passes)
+ *   pass_kinds -- 1 sweep, 2 tile, 3 gather for each pass
+ * Returns QSIM_EINVAL for invalid steps or when an output would exceed cap. */
+int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, int strategy,
+                      int tile_bits, int low_bits, int scratch_available, qsim_plan_stats *stats,
+                      uint64_t *order, uint64_t *pass_ends, uint32_t *pass_kinds, size_t cap);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* Message describing the last error on this host thread ("" if none). */
+const char *qsim_last_error(void);
+
+/* Library version string. */
+const char *qsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,294 @@
+"""Thin Python binding of libqsim.so (include/qsim.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels.  There is
+no CPU fallback: if the library is missing or cannot load, constructing a
+``Simulator`` raises ``QsimError``.
+
+    sim = Simulator(M=16, dtype=np.complex128)      # state + scratch from torch
+    sim.load_state(k1)                              # numpy, 2^M amplitudes
+    sim.apply(steps)                                # workloads.STEP_DTYPE array
+    k2 = sim.read_state()
+    p, norm = sim.probabilities(with_norm=True)     # FP64
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .workloads import STEP_DTYPE
+
+QSIM_OK = 0
+QSIM_EINVAL = -1
+QSIM_ENOMEM = -2
+QSIM_ECUDA = -3
+QSIM_ETIMEOUT = -4
+QSIM_EBUSY = -5
+QSIM_ENOTFOUND = -6
+
+QSIM_C64 = 0
+QSIM_C128 = 1
+
+STRATEGY = {"auto": 0, "sweep": 1, "tile": 2, "gather": 3, "inplace": 4}
+PASS_KIND = {1: "sweep", 2: "tile", 3: "gather"}
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libqsim.so")
+
+# every symbol include/qsim.h declares
+EXPORTS = (
+    "qsim_create", "qsim_create_with_buffers", "qsim_destroy", "qsim_load_state",
+    "qsim_read_state", "qsim_state_device", "qsim_apply_circuit", "qsim_set_strategy",
+    "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times",
+    "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
+    "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
+)
+
+
+class QsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("qsim error %d: %s" % (code, msg))
+        self.code = code
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("steps_in", ctypes.c_uint64), ("steps_cancelled", ctypes.c_uint64),
+                ("passes", ctypes.c_uint64), ("sweep_passes", ctypes.c_uint64),
+                ("tile_passes", ctypes.c_uint64), ("gather_passes", ctypes.c_uint64),
+                ("algorithmic_bytes", ctypes.c_double), ("full_pass_equiv", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libqsim.so (built by ``paper_quant_ph_0308158_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise QsimError(QSIM_EINVAL, "libqsim.so is not built (%s); run "
+                            "paper_quant_ph_0308158_gb300.build.build()" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        p, i, u32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "qsim_create": ([u32, i, pp], i),
+            "qsim_create_with_buffers": ([u32, i, p, p, p, pp], i),
+            "qsim_destroy": ([p], None),
+            "qsim_load_state": ([p, p, sz], i),
+            "qsim_read_state": ([p, p, sz], i),
+            "qsim_state_device": ([p], p),
+            "qsim_apply_circuit": ([p, p, sz], i),
+            "qsim_set_strategy": ([p, i, i, i], i),
+            "qsim_set_canonicalize": ([p, i], i),
+            "qsim_set_profiling": ([p, i], i),
+            "qsim_get_pass_times": ([p, p, p, p, sz, ctypes.POINTER(sz)], i),
+            "qsim_get_plan_stats": ([p, ctypes.POINTER(PlanStats)], i),
+            "qsim_synchronize": ([p], i),
+            "qsim_probabilities": ([p, p, sz, ctypes.POINTER(ctypes.c_double)], i),
+            "qsim_probabilities_device": ([p, p, ctypes.POINTER(ctypes.c_double)], i),
+            "qsim_plan_circuit": ([u32, i, p, sz, i, i, i, i, ctypes.POINTER(PlanStats), p, p, p, sz], i),
+            "qsim_last_error": ([], ctypes.c_char_p),
+            "qsim_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != QSIM_OK:
+        msg = load().qsim_last_error()
+        raise QsimError(rc, msg.decode() if msg else "")
+
+
+def dtype_code(dtype) -> int:
+    dt = np.dtype(dtype)
+    if dt == np.complex64:
+        return QSIM_C64
+    if dt == np.complex128:
+        return QSIM_C128
+    raise QsimError(QSIM_EINVAL, "dtype must be complex64 or complex128")
+
+
+def as_steps(steps) -> np.ndarray:
+    s = np.ascontiguousarray(steps)
+    if s.dtype != STEP_DTYPE:
+        raise QsimError(QSIM_EINVAL, "steps must be a workloads.STEP_DTYPE array")
+    return s
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+def plan_circuit(M: int, dtype, steps, strategy: str = "auto", tile_bits: int = 0,
+                 low_bits: int = 0, scratch: bool = True) -> dict:
+    """Host-only planning (no GPU): pass kinds, pass boundaries, applied order."""
+    L = load()
+    s = as_steps(steps)
+    cap = max(len(s), 1)
+    order = np.zeros(cap, dtype=np.uint64)
+    ends = np.zeros(cap, dtype=np.uint64)
+    kinds = np.zeros(cap, dtype=np.uint32)
+    st = PlanStats()
+    _check(L.qsim_plan_circuit(M, dtype_code(dtype), _ptr(s), len(s), STRATEGY[strategy],
+                               tile_bits, low_bits, int(scratch), ctypes.byref(st),
+                               _ptr(order), _ptr(ends), _ptr(kinds), cap))
+    n_pass = int(st.passes)
+    n_ord = int(st.steps_in - st.steps_cancelled)
+    return dict(stats=st.as_dict(), order=order[:n_ord].copy(), pass_ends=ends[:n_pass].copy(),
+                kinds=[PASS_KIND[int(k)] for k in kinds[:n_pass]])
+
+
+class Simulator:
+    """A 2^M-amplitude state on the current CUDA device.
+
+    ``buffers="torch"`` (default) takes the state and scratch buffers from the
+    PyTorch caching allocator and runs on torch's current stream;
+    ``buffers="library"`` lets libqsim allocate them (cudaMalloc) on its own
+    stream.  ``scratch=False`` keeps every pass in place.
+    """
+
+    def __init__(self, M: int, dtype=np.complex128, buffers: str = "torch",
+                 scratch: bool = True):
+        self.M = int(M)
+        self.dtype = np.dtype(dtype)
+        self.n = 1 << self.M
+        self._lib = load()
+        self._ctx = ctypes.c_void_p()
+        self._tensors = []
+        code = dtype_code(self.dtype)
+        if buffers == "torch":
+            import torch
+            tdt = torch.complex64 if code == QSIM_C64 else torch.complex128
+            st = torch.empty(self.n, dtype=tdt, device="cuda")
+            st.zero_()
+            sc = torch.empty(self.n, dtype=tdt, device="cuda") if scratch else None
+            self._tensors = [st, sc]
+            stream = torch.cuda.current_stream().cuda_stream
+            _check(self._lib.qsim_create_with_buffers(
+                self.M, code, ctypes.c_void_p(st.data_ptr()),
+                ctypes.c_void_p(sc.data_ptr() if sc is not None else 0),
+                ctypes.c_void_p(stream), ctypes.byref(self._ctx)))
+        elif buffers == "library":
+            _check(self._lib.qsim_create(self.M, code, ctypes.byref(self._ctx)))
+            if not scratch:
+                self.set_strategy("inplace")
+        else:
+            raise QsimError(QSIM_EINVAL, "buffers must be 'torch' or 'library'")
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if self._ctx:
+            self._lib.qsim_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+        self._tensors = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ------------------------------------------------------------------
+    def load_state(self, k1: np.ndarray):
+        a = np.ascontiguousarray(k1, dtype=self.dtype)
+        if a.shape != (self.n,):
+            raise QsimError(QSIM_EINVAL, "state must have 2^M amplitudes")
+        _check(self._lib.qsim_load_state(self._ctx, _ptr(a), self.n))
+
+    def read_state(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n, dtype=self.dtype)
+        _check(self._lib.qsim_read_state(self._ctx, _ptr(out), self.n))
+        return out
+
+    def state_ptr(self) -> int:
+        return int(self._lib.qsim_state_device(self._ctx) or 0)
+
+    def state_tensor(self):
+        """The torch tensor that currently holds the state (torch buffers only)."""
+        ptr = self.state_ptr()
+        for t in self._tensors:
+            if t is not None and t.data_ptr() == ptr:
+                return t
+        raise QsimError(QSIM_EINVAL, "state is not in a torch-owned buffer")
+
+    # -- circuits -----------------------------------------------------------------
+    def set_strategy(self, strategy: str = "auto", tile_bits: int = 0, low_bits: int = 0):
+        _check(self._lib.qsim_set_strategy(self._ctx, STRATEGY[strategy], tile_bits, low_bits))
+
+    def set_canonicalize(self, enable: bool):
+        _check(self._lib.qsim_set_canonicalize(self._ctx, int(bool(enable))))
+
+    def apply(self, steps):
+        s = as_steps(steps)
+        _check(self._lib.qsim_apply_circuit(self._ctx, _ptr(s), len(s)))
+
+    def set_profiling(self, enable: bool):
+        _check(self._lib.qsim_set_profiling(self._ctx, int(bool(enable))))
+
+    def pass_times(self):
+        """[(kind, ms, algorithmic bytes)] for every pass recorded since the
+        last call (profiling must be on); clears the record."""
+        n = ctypes.c_size_t(0)
+        _check(self._lib.qsim_get_pass_times(self._ctx, None, None, None, 0, ctypes.byref(n)))
+        k = int(n.value)
+        ms = np.zeros(max(k, 1), np.float64)
+        kinds = np.zeros(max(k, 1), np.uint32)
+        by = np.zeros(max(k, 1), np.float64)
+        _check(self._lib.qsim_get_pass_times(self._ctx, _ptr(ms), _ptr(kinds), _ptr(by), k,
+                                             ctypes.byref(n)))
+        return [(PASS_KIND[int(kinds[i])], float(ms[i]), float(by[i])) for i in range(k)]
+
+    def plan_stats(self) -> dict:
+        st = PlanStats()
+        _check(self._lib.qsim_get_plan_stats(self._ctx, ctypes.byref(st)))
+        return st.as_dict()
+
+    def synchronize(self):
+        _check(self._lib.qsim_synchronize(self._ctx))
+
+    # -- post-processing --------------------------------------------------------------
+    def probabilities(self, with_norm: bool = False, out: np.ndarray | None = None):
+        """FP64 probabilities in host memory (``out``: optional float64 buffer,
+        e.g. pinned, of 2^M entries)."""
+        p = np.empty(self.n, dtype=np.float64) if out is None else out
+        if p.dtype != np.float64 or p.shape != (self.n,) or not p.flags.c_contiguous:
+            raise QsimError(QSIM_EINVAL, "out must be a contiguous float64 array of 2^M entries")
+        norm = ctypes.c_double(0.0)
+        _check(self._lib.qsim_probabilities(self._ctx, _ptr(p), self.n,
+                                            ctypes.byref(norm) if with_norm else None))
+        return (p, norm.value) if with_norm else p
+
+    def probabilities_device(self, out_ptr: int, with_norm: bool = False):
+        """FP64 probabilities into device memory at out_ptr (2^M doubles)."""
+        norm = ctypes.c_double(0.0)
+        _check(self._lib.qsim_probabilities_device(self._ctx, ctypes.c_void_p(out_ptr),
+                                                   ctypes.byref(norm) if with_norm else None))
+        return norm.value if with_norm else None
+
+
+def version() -> str:
+    return load().qsim_version().decode()

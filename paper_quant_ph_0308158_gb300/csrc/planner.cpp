@@ -1,0 +1,448 @@
+// planner.cpp -- host side of the engine: step validation, canonicalisation,
+// segmentation of the wiring diagram into passes, and the per-pass tables the
+// kernels read.
+//
+// Passes (see qsim_internal.h):
+//   * TILE passes apply runs of steps whose targets lie in one tile of k
+//     address bits (the lowest l bits, which give contiguous runs of 2^l
+//     amplitudes, plus up to k-l chosen higher bits).  Segments are grown
+//     greedily in circuit order; a later step may join an earlier segment when
+//     it commutes with every step it overtakes (Sec. 2i notes that steps can
+//     be grouped; two steps commute when neither's target is a control of the
+//     other, since each then leaves the other's control bits unchanged).
+//   * SWEEP passes apply one step over its toggled pairs only (Sec. 2b).
+//   * GATHER passes evaluate the inverse wiring diagram on every output index
+//     (Sec. 2h product, then the gather k2(i) = k1(x(i))): as a GF(2) affine
+//     map when the segment has only NOT/CNOT steps, otherwise step by step in
+//     bit-sliced form.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "qsim_internal.h"
+
+namespace qsim {
+
+namespace {
+
+inline int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+inline uint64_t full_mask(uint32_t M) { return M >= 64 ? ~0ull : ((1ull << M) - 1ull); }
+
+bool same_step(const qsim_step &a, const qsim_step &b)
+{
+    return a.target == b.target && a.ctrl_mask == b.ctrl_mask && a.ctrl_pol == b.ctrl_pol;
+}
+
+// splitmix64: deterministic sampling of tile ids for the touched-fraction estimate.
+uint64_t splitmix64(uint64_t &s)
+{
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+int validate_steps(uint32_t M, const qsim_step *steps, size_t L, std::string *msg)
+{
+    if (M < 1 || M > QSIM_MAX_QUBITS) {
+        if (msg) *msg = "M must be in [1, " + std::to_string(QSIM_MAX_QUBITS) + "]";
+        return QSIM_EINVAL;
+    }
+    if (L > 0 && steps == nullptr) {
+        if (msg) *msg = "steps is NULL";
+        return QSIM_EINVAL;
+    }
+    const uint64_t all = full_mask(M);
+    for (size_t i = 0; i < L; ++i) {
+        const qsim_step &s = steps[i];
+        const char *why = nullptr;
+        if (s.target >= M)
+            why = "target bit >= M";
+        else if (s.reserved != 0)
+            why = "reserved field is not zero";
+        else if (s.ctrl_mask & ~all)
+            why = "control bit >= M";
+        else if ((s.ctrl_mask >> s.target) & 1ull)
+            why = "target bit is also a control";
+        else if (s.ctrl_pol & ~s.ctrl_mask)
+            why = "polarity bit outside the control mask";
+        if (why) {
+            if (msg) *msg = "step " + std::to_string(i) + ": " + why;
+            return QSIM_EINVAL;
+        }
+    }
+    return QSIM_OK;
+}
+
+namespace {
+
+// Adjacent equal steps cancel (each step matrix is its own inverse, Sec. 2a).
+// A stack removes nested pairs too (A B B A -> nothing).
+std::vector<uint64_t> canonical_order(const qsim_step *steps, size_t L, bool cancel,
+                                      uint64_t *cancelled)
+{
+    std::vector<uint64_t> st;
+    st.reserve(L);
+    for (size_t i = 0; i < L; ++i) {
+        if (cancel && !st.empty() && same_step(steps[st.back()], steps[i]))
+            st.pop_back();
+        else
+            st.push_back(i);
+    }
+    *cancelled = L - st.size();
+    return st;
+}
+
+double state_bytes(uint32_t M, size_t amp) { return (double)amp * (double)(1ull << M); }
+
+Pass make_sweep(uint32_t M, const qsim_step &s, size_t amp)
+{
+    Pass p{};
+    p.kind = kSweep;
+    p.nsteps = 1;
+    const int c = popcount64(s.ctrl_mask);
+    p.sweep.n_pairs = 1ull << (M - 1 - c);
+    p.sweep.pol = s.ctrl_pol;
+    p.sweep.half = 1ull << s.target;
+    uint64_t ins = s.ctrl_mask | (1ull << s.target);
+    uint32_t n = 0;
+    while (ins) {
+        p.sweep.ins[n++] = (uint32_t)__builtin_ctzll(ins);
+        ins &= ins - 1;
+    }
+    p.sweep.nins = n;
+    p.alg_bytes = 2.0 * (double)amp * (double)(1ull << (M - c));
+    return p;
+}
+
+struct TileGeom {
+    uint32_t k, l, nh_max;
+};
+
+TileGeom tile_geometry(uint32_t M, const PlanOptions &o)
+{
+    TileGeom g;
+    const uint32_t kdef = o.amp_bytes == 16 ? 12 : 13;
+    const uint32_t ldef = o.amp_bytes == 16 ? 4 : 5;
+    uint32_t k = o.tile_bits > 0 ? (uint32_t)o.tile_bits : kdef;
+    uint32_t l = o.low_bits > 0 ? (uint32_t)o.low_bits : ldef;
+    k = std::min<uint32_t>(std::min<uint32_t>(k, kMaxTileBits), M);
+    while (k > 1 && (o.amp_bytes << k) > kMaxTileBytes) --k;  // one tile fits shared memory
+    l = std::min(l, k);
+    if (o.amp_bytes == 8 && l < 1) l = 1;  // bulk copies move >= 16 bytes
+    if (k < l) k = l;
+    g.k = k;
+    g.l = l;
+    g.nh_max = std::min<uint32_t>(k - l, kMaxHighBits);
+    g.k = g.l + g.nh_max;
+    return g;
+}
+
+// Build one tile pass for the given step indices and high-bit set.
+void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &seg,
+               uint64_t high_mask, const TileGeom &g, const PlanOptions &o, Plan *plan)
+{
+    Pass p{};
+    p.kind = kTile;
+    TilePass &t = p.tile;
+    // pad the high set with unused bits so the tile always has k bits when M allows
+    uint32_t want = std::min<uint32_t>(g.nh_max, M - g.l);
+    for (uint32_t b = g.l; b < M && (uint32_t)popcount64(high_mask) < want; ++b)
+        high_mask |= 1ull << b;
+    t.l = g.l;
+    t.nh = 0;
+    int8_t g2l[64];
+    for (int b = 0; b < 64; ++b) g2l[b] = -1;
+    for (uint32_t b = 0; b < g.l; ++b) g2l[b] = (int8_t)b;
+    for (uint64_t h = high_mask; h; h &= h - 1) {
+        const uint32_t b = (uint32_t)__builtin_ctzll(h);
+        g2l[b] = (int8_t)(g.l + t.nh);
+        t.high[t.nh++] = b;
+    }
+    t.k = t.l + t.nh;
+    t.n_tiles = 1ull << (M - t.k);
+    t.step_off = (uint32_t)plan->tile_steps.size();
+    t.nsteps = (uint32_t)seg.size();
+    const uint64_t tile_mask = ((1ull << g.l) - 1ull) | high_mask;
+    bool all_local = true;
+    for (uint64_t idx : seg) {
+        const qsim_step &s = steps[idx];
+        TileStep ts{};
+        for (uint64_t c = s.ctrl_mask & tile_mask; c; c &= c - 1) {
+            const uint32_t b = (uint32_t)__builtin_ctzll(c);
+            ts.cl |= 1u << g2l[b];
+            if ((s.ctrl_pol >> b) & 1ull) ts.pl |= 1u << g2l[b];
+        }
+        ts.tmask = 1u << g2l[s.target];
+        ts.co = s.ctrl_mask & ~tile_mask;
+        ts.po = s.ctrl_pol & ~tile_mask;
+        if (ts.co) all_local = false;
+        plan->tile_steps.push_back(ts);
+    }
+    t.all_local = all_local ? 1u : 0u;
+    // fraction of tiles that have at least one active step
+    double touched = 1.0;
+    if (!all_local) {
+        const int samples = 512;
+        int hit = 0;
+        uint64_t seed = 0x5eed0000ull + plan->passes.size();
+        for (int i = 0; i < samples; ++i) {
+            const uint64_t tile = splitmix64(seed) & (t.n_tiles - 1);
+            uint64_t base = tile << g.l;
+            for (uint32_t q = 0; q < t.nh; ++q) {
+                const uint32_t pos = t.high[q];
+                base = ((base >> pos) << (pos + 1)) | (base & ((1ull << pos) - 1ull));
+            }
+            for (uint32_t j = 0; j < t.nsteps; ++j) {
+                const TileStep &ts = plan->tile_steps[t.step_off + j];
+                if ((base & ts.co) == ts.po) {
+                    ++hit;
+                    break;
+                }
+            }
+        }
+        touched = (double)hit / samples;
+    }
+    t.touched = touched;
+    p.nsteps = t.nsteps;
+    p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes) * touched;
+    plan->passes.push_back(p);
+}
+
+// Greedy, commutation-aware tile segmentation of 'order' (circuit indices).
+void plan_tiles(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &order,
+                const PlanOptions &o, bool sweep_singles, Plan *plan)
+{
+    const TileGeom g = tile_geometry(M, o);
+    const uint64_t low_mask = (1ull << g.l) - 1ull;
+    const size_t n = order.size();
+    std::vector<char> done(n, 0);
+    size_t first = 0;
+    while (first < n) {
+        std::vector<uint64_t> seg;
+        std::vector<size_t> seg_pos;
+        uint64_t high = 0;
+        uint64_t def_targets = 0, def_controls = 0;  // unions over overtaken steps
+        int scanned = 0, deferred = 0;
+        for (size_t j = first; j < n && scanned < o.lookahead; ++j) {
+            if (done[j]) continue;
+            ++scanned;
+            const qsim_step &s = steps[order[j]];
+            const uint64_t tb = 1ull << s.target;
+            const bool commutes = !(def_controls & tb) && !(def_targets & s.ctrl_mask);
+            bool take = false;
+            if (commutes) {
+                if ((tb & low_mask) || (tb & high)) {
+                    take = true;
+                } else if ((uint32_t)popcount64(high) < g.nh_max) {
+                    high |= tb;
+                    take = true;
+                }
+            }
+            if (take) {
+                seg.push_back(order[j]);
+                seg_pos.push_back(j);
+                if ((int)seg.size() >= kMaxTileSteps) break;
+            } else {
+                def_targets |= tb;
+                def_controls |= s.ctrl_mask;
+                if (++deferred > 96 || (def_targets | def_controls) == full_mask(M)) break;
+            }
+        }
+        for (size_t j : seg_pos) done[j] = 1;
+        if (seg.size() == 1 && sweep_singles) {
+            plan->passes.push_back(make_sweep(M, steps[seg[0]], o.amp_bytes));
+        } else {
+            emit_tile(M, steps, seg, high, g, o, plan);
+        }
+        for (uint64_t idx : seg) plan->order.push_back(idx);
+        plan->pass_ends.push_back(plan->order.size());
+        while (first < n && done[first]) ++first;
+    }
+}
+
+bool is_affine_step(const qsim_step &s) { return popcount64(s.ctrl_mask) <= 1; }
+
+// GF(2) affine map x(i) = A i ^ b of the inverse of a NOT/CNOT segment:
+// x = g_1(g_2(... g_n(i))), built by composing each step onto the outputs of
+// the map so far, last step first.  Stored as per-byte XOR tables.
+void emit_affine(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &seg,
+                 const PlanOptions &o, Plan *plan)
+{
+    uint64_t row[64];  // row[t]: input bits that XOR into output bit t
+    uint64_t bvec = 0;
+    for (uint32_t t = 0; t < M; ++t) row[t] = 1ull << t;
+    for (size_t q = seg.size(); q-- > 0;) {
+        const qsim_step &s = steps[seg[q]];
+        const uint32_t t = s.target;
+        if (s.ctrl_mask == 0) {
+            bvec ^= 1ull << t;
+        } else {
+            const uint32_t c = (uint32_t)__builtin_ctzll(s.ctrl_mask);
+            row[t] ^= row[c];
+            const uint64_t bc = (bvec >> c) & 1ull;
+            const uint64_t flip = bc ^ (((s.ctrl_pol >> c) & 1ull) ? 0ull : 1ull);
+            bvec ^= flip << t;
+        }
+    }
+    uint64_t col[64];
+    for (uint32_t j = 0; j < M; ++j) {
+        uint64_t c = 0;
+        for (uint32_t t = 0; t < M; ++t) c |= ((row[t] >> j) & 1ull) << t;
+        col[j] = c;
+    }
+    Pass p{};
+    p.kind = kGather;
+    GatherPass &gp = p.gather;
+    gp.affine = 1;
+    gp.nbytes = (M + 7) / 8;
+    gp.table_off = (uint32_t)plan->gather_tables.size();
+    gp.bvec = bvec;
+    for (uint32_t b = 0; b < gp.nbytes; ++b) {
+        for (uint32_t v = 0; v < 256; ++v) {
+            uint64_t x = 0;
+            for (uint32_t j = 0; j < 8; ++j)
+                if (((v >> j) & 1u) && 8 * b + j < M) x ^= col[8 * b + j];
+            plan->gather_tables.push_back(x);
+        }
+    }
+    p.nsteps = (uint32_t)seg.size();
+    p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+    plan->passes.push_back(p);
+}
+
+void emit_sliced(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &seg,
+                 const PlanOptions &o, Plan *plan)
+{
+    Pass p{};
+    p.kind = kGather;
+    GatherPass &gp = p.gather;
+    gp.affine = 0;
+    gp.step_off = (uint32_t)plan->sliced_steps.size();
+    gp.nsteps = (uint32_t)seg.size();
+    for (size_t q = 0; q < seg.size(); ++q) {
+        const qsim_step &s = steps[seg[q]];
+        SlicedStep h{};
+        h.t_off = (uint16_t)(s.target * kSlicedThreads * 4);
+        int c = 0;
+        for (uint64_t m = s.ctrl_mask; m; m &= m - 1) {
+            const uint32_t b = (uint32_t)__builtin_ctzll(m);
+            h.c_off[c] = (uint16_t)(b * kSlicedThreads * 4);
+            if (!((s.ctrl_pol >> b) & 1ull)) h.neg |= (uint8_t)(1u << c);
+            ++c;
+        }
+        h.nc = (uint8_t)c;
+        plan->sliced_steps.push_back(h);
+    }
+    p.nsteps = (uint32_t)seg.size();
+    p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+    plan->passes.push_back(p);
+}
+
+// Gather segmentation: maximal runs; affine runs use tables, others bit-sliced.
+// Steps with more controls than the sliced descriptor holds run as sweeps.
+void plan_gather(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &order,
+                 const PlanOptions &o, Plan *plan)
+{
+    size_t i = 0;
+    const size_t n = order.size();
+    while (i < n) {
+        const qsim_step &s0 = steps[order[i]];
+        if (popcount64(s0.ctrl_mask) > kSlicedMaxControls) {
+            plan->passes.push_back(make_sweep(M, s0, o.amp_bytes));
+            plan->order.push_back(order[i]);
+            plan->pass_ends.push_back(plan->order.size());
+            ++i;
+            continue;
+        }
+        size_t j = i;
+        bool affine = true;
+        while (j < n && (j - i) < (size_t)kMaxGatherSteps &&
+               popcount64(steps[order[j]].ctrl_mask) <= kSlicedMaxControls) {
+            affine = affine && is_affine_step(steps[order[j]]);
+            ++j;
+        }
+        std::vector<uint64_t> seg(order.begin() + i, order.begin() + j);
+        if (affine)
+            emit_affine(M, steps, seg, o, plan);
+        else
+            emit_sliced(M, steps, seg, o, plan);
+        for (uint64_t idx : seg) plan->order.push_back(idx);
+        plan->pass_ends.push_back(plan->order.size());
+        i = j;
+    }
+}
+
+}  // namespace
+
+int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o, Plan *plan,
+              std::string *msg)
+{
+    int rc = validate_steps(M, steps, L, msg);
+    if (rc != QSIM_OK) return rc;
+    if (o.amp_bytes != 8 && o.amp_bytes != 16) {
+        if (msg) *msg = "amplitude size must be 8 or 16 bytes";
+        return QSIM_EINVAL;
+    }
+    *plan = Plan{};
+    plan->steps_in = L;
+    std::vector<uint64_t> order = canonical_order(steps, L, o.cancel_adjacent, &plan->cancelled);
+    if (order.empty()) return QSIM_OK;
+
+    int strategy = o.strategy;
+    PlanOptions oo = o;
+    if (strategy == QSIM_STRATEGY_INPLACE) {
+        strategy = QSIM_STRATEGY_AUTO;
+        oo.scratch_available = false;
+    }
+    if (strategy == QSIM_STRATEGY_GATHER && !o.scratch_available) {
+        if (msg) *msg = "gather strategy needs a scratch buffer";
+        return QSIM_EINVAL;
+    }
+    if (strategy == QSIM_STRATEGY_SWEEP) {
+        for (uint64_t idx : order) {
+            plan->passes.push_back(make_sweep(M, steps[idx], oo.amp_bytes));
+            plan->order.push_back(idx);
+            plan->pass_ends.push_back(plan->order.size());
+        }
+        return QSIM_OK;
+    }
+    if (strategy == QSIM_STRATEGY_TILE) {
+        plan_tiles(M, steps, order, oo, false, plan);
+        return QSIM_OK;
+    }
+    if (strategy == QSIM_STRATEGY_GATHER) {
+        plan_gather(M, steps, order, oo, plan);
+        return QSIM_OK;
+    }
+    // AUTO: in-place tile/sweep plan, replaced by gather passes when a
+    // scratch buffer is allowed and the gather plan moves fewer bytes.
+    Plan tp;
+    tp.steps_in = plan->steps_in;
+    tp.cancelled = plan->cancelled;
+    plan_tiles(M, steps, order, oo, true, &tp);
+    if (oo.scratch_available) {
+        Plan gp;
+        gp.steps_in = plan->steps_in;
+        gp.cancelled = plan->cancelled;
+        plan_gather(M, steps, order, oo, &gp);
+        // A gather pass reads scattered amplitudes: charge the sector
+        // over-fetch (32-byte sectors) on its reads.
+        const double over = std::max(1.0, 32.0 / (double)oo.amp_bytes);
+        double tcost = 0, gcost = 0;
+        for (const Pass &p : tp.passes) tcost += p.alg_bytes;
+        for (const Pass &p : gp.passes)
+            gcost += p.kind == kGather ? p.alg_bytes * (over + 1.0) / 2.0 : p.alg_bytes;
+        if (gcost < tcost) {
+            *plan = std::move(gp);
+            return QSIM_OK;
+        }
+    }
+    *plan = std::move(tp);
+    return QSIM_OK;
+}
+
+}  // namespace qsim

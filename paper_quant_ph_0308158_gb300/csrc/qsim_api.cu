@@ -1,0 +1,498 @@
+// qsim_api.cu -- the C ABI (include/qsim.h): contexts, state transfer,
+// circuit application and probabilities.  Host code only; kernels live in
+// kernels.cu and the planner in planner.cpp.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qsim_internal.h"
+
+using namespace qsim;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? QSIM_ENOMEM : QSIM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QSIM_CUDA(call, what)                       \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t amp_bytes_of(int dtype) { return dtype == QSIM_C64 ? 8 : dtype == QSIM_C128 ? 16 : 0; }
+
+constexpr size_t kProbChunk = size_t(1) << 24;  // amplitudes per host-probability chunk
+
+}  // namespace
+
+struct qsim_ctx {
+    uint32_t M = 0;
+    int dtype = 0;
+    size_t amp = 0;
+    uint64_t n = 0;
+    int device = 0;
+    void *buf[2] = {nullptr, nullptr};
+    bool own[2] = {false, false};
+    int cur = 0;
+    bool external = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int *d_err = nullptr;
+    // plan tables: device copy and pinned host staging
+    char *d_plan = nullptr;
+    size_t d_plan_cap = 0;
+    char *h_plan = nullptr;
+    size_t h_plan_cap = 0;
+    cudaEvent_t plan_ev = nullptr;
+    bool plan_ev_pending = false;
+    double *d_partials = nullptr;
+    double *d_norms = nullptr;
+    double *d_probs_chunk = nullptr;
+    PlanOptions opts;
+    qsim_plan_stats stats{};
+    // tracing: events around each pass of the last apply
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;        // 2 per pass
+    std::vector<uint32_t> prof_kinds;
+    std::vector<double> prof_bytes;
+};
+
+namespace {
+
+int ctx_init_common(qsim_ctx *c)
+{
+    QSIM_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
+    QSIM_CUDA(cudaMalloc(&c->d_err, sizeof(int)), "cudaMalloc(error flag)");
+    QSIM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)), "cudaMemset(error flag)");
+    const int np = probabilities_partials_needed();
+    QSIM_CUDA(cudaMalloc(&c->d_partials, sizeof(double) * np), "cudaMalloc(partials)");
+    const size_t nchunks = (c->n + kProbChunk - 1) / kProbChunk;
+    QSIM_CUDA(cudaMalloc(&c->d_norms, sizeof(double) * (nchunks + 1)), "cudaMalloc(norms)");
+    QSIM_CUDA(cudaEventCreateWithFlags(&c->plan_ev, cudaEventDisableTiming), "cudaEventCreate");
+    c->opts.amp_bytes = c->amp;
+    return QSIM_OK;
+}
+
+void ctx_free(qsim_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i)
+        if (c->own[i] && c->buf[i]) cudaFree(c->buf[i]);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_plan) cudaFree(c->d_plan);
+    if (c->h_plan) cudaFreeHost(c->h_plan);
+    if (c->plan_ev) cudaEventDestroy(c->plan_ev);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_norms) cudaFree(c->d_norms);
+    if (c->d_probs_chunk) cudaFree(c->d_probs_chunk);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// Read and clear the device error flag (waits for the stream).
+int check_device(qsim_ctx *c)
+{
+    QSIM_CUDA(cudaStreamSynchronize(c->stream), "kernel execution");
+    int flag = 0;
+    QSIM_CUDA(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        return fail(QSIM_ETIMEOUT, "a bounded device wait gave up (error flag " +
+                                       std::to_string(flag) + ")");
+    }
+    return QSIM_OK;
+}
+
+int ensure_scratch(qsim_ctx *c)
+{
+    const int other = 1 - c->cur;
+    if (c->buf[other]) return QSIM_OK;
+    if (c->external) return fail(QSIM_EINVAL, "no scratch buffer was given to this context");
+    QSIM_CUDA(cudaMalloc(&c->buf[other], c->amp * c->n), "cudaMalloc(scratch state)");
+    c->own[other] = true;
+    return QSIM_OK;
+}
+
+int ensure_plan_buffers(qsim_ctx *c, size_t bytes)
+{
+    if (c->plan_ev_pending) {
+        QSIM_CUDA(cudaEventSynchronize(c->plan_ev), "plan staging reuse");
+        c->plan_ev_pending = false;
+    }
+    if (bytes > c->h_plan_cap) {
+        if (c->h_plan) cudaFreeHost(c->h_plan);
+        c->h_plan = nullptr;
+        size_t cap = bytes + bytes / 2 + 4096;
+        QSIM_CUDA(cudaMallocHost(&c->h_plan, cap), "cudaMallocHost(plan staging)");
+        c->h_plan_cap = cap;
+    }
+    if (bytes > c->d_plan_cap) {
+        // previous kernels on the stream may still read the old table
+        QSIM_CUDA(cudaStreamSynchronize(c->stream), "plan table resize");
+        if (c->d_plan) cudaFree(c->d_plan);
+        c->d_plan = nullptr;
+        size_t cap = bytes + bytes / 2 + 4096;
+        QSIM_CUDA(cudaMalloc(&c->d_plan, cap), "cudaMalloc(plan tables)");
+        c->d_plan_cap = cap;
+    }
+    return QSIM_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void fill_stats(const Plan &plan, uint32_t M, size_t amp, qsim_plan_stats *st)
+{
+    std::memset(st, 0, sizeof(*st));
+    st->steps_in = plan.steps_in;
+    st->steps_cancelled = plan.cancelled;
+    st->passes = plan.passes.size();
+    for (const Pass &p : plan.passes) {
+        if (p.kind == kSweep) ++st->sweep_passes;
+        if (p.kind == kTile) ++st->tile_passes;
+        if (p.kind == kGather) ++st->gather_passes;
+        st->algorithmic_bytes += p.alg_bytes;
+    }
+    st->full_pass_equiv = st->algorithmic_bytes / (2.0 * (double)amp * (double)(1ull << M));
+}
+
+int plan_options(int strategy, int tile_bits, int low_bits, PlanOptions *o)
+{
+    if (strategy < QSIM_STRATEGY_AUTO || strategy > QSIM_STRATEGY_INPLACE)
+        return fail(QSIM_EINVAL, "unknown strategy");
+    if (tile_bits < 0 || tile_bits > kMaxTileBits) return fail(QSIM_EINVAL, "tile_bits out of range");
+    if (low_bits < 0 || low_bits > kMaxTileBits) return fail(QSIM_EINVAL, "low_bits out of range");
+    o->strategy = strategy;
+    o->tile_bits = tile_bits;
+    o->low_bits = low_bits;
+    return QSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qsim_create(uint32_t M, int dtype, qsim_ctx **out)
+{
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (M < 1 || M > QSIM_MAX_QUBITS) return fail(QSIM_EINVAL, "M out of range");
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    qsim_ctx *c = new qsim_ctx;
+    c->M = M;
+    c->dtype = dtype;
+    c->amp = amp;
+    c->n = 1ull << M;
+    int rc = ctx_init_common(c);
+    if (rc == QSIM_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
+        c->own_stream = (e == cudaSuccess);
+    }
+    if (rc == QSIM_OK) {
+        cudaError_t e = cudaMalloc(&c->buf[0], amp * c->n);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(state)");
+        else {
+            c->own[0] = true;
+            e = cudaMemsetAsync(c->buf[0], 0, amp * c->n, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset(state)");
+        }
+    }
+    if (rc != QSIM_OK) {
+        ctx_free(c);
+        return rc;
+    }
+    c->opts.scratch_available = true;  // allocated on first gather pass
+    *out = c;
+    return QSIM_OK;
+}
+
+int qsim_create_with_buffers(uint32_t M, int dtype, void *d_state, void *d_scratch, void *stream,
+                             qsim_ctx **out)
+{
+    if (!out) return fail(QSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (M < 1 || M > QSIM_MAX_QUBITS) return fail(QSIM_EINVAL, "M out of range");
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    if (!d_state) return fail(QSIM_EINVAL, "d_state is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_state) & 255u) ||
+        (reinterpret_cast<uintptr_t>(d_scratch) & 255u))
+        return fail(QSIM_EINVAL, "device buffers must be 256-byte aligned");
+    if (d_scratch == d_state) return fail(QSIM_EINVAL, "scratch must differ from the state buffer");
+    qsim_ctx *c = new qsim_ctx;
+    c->M = M;
+    c->dtype = dtype;
+    c->amp = amp;
+    c->n = 1ull << M;
+    c->external = true;
+    c->buf[0] = d_state;
+    c->buf[1] = d_scratch;
+    c->stream = static_cast<cudaStream_t>(stream);
+    int rc = ctx_init_common(c);
+    if (rc != QSIM_OK) {
+        ctx_free(c);
+        return rc;
+    }
+    c->opts.scratch_available = d_scratch != nullptr;
+    *out = c;
+    return QSIM_OK;
+}
+
+void qsim_destroy(qsim_ctx *ctx) { ctx_free(ctx); }
+
+void *qsim_state_device(qsim_ctx *ctx) { return ctx ? ctx->buf[ctx->cur] : nullptr; }
+
+int qsim_load_state(qsim_ctx *c, const void *host, size_t n_amps)
+{
+    if (!c || !host) return fail(QSIM_EINVAL, "NULL argument");
+    if (n_amps != c->n) return fail(QSIM_EINVAL, "n_amps must equal 2^M");
+    QSIM_CUDA(cudaMemcpyAsync(c->buf[c->cur], host, c->amp * c->n, cudaMemcpyHostToDevice, c->stream),
+              "cudaMemcpy(load state)");
+    QSIM_CUDA(cudaStreamSynchronize(c->stream), "cudaMemcpy(load state)");
+    return QSIM_OK;
+}
+
+int qsim_read_state(qsim_ctx *c, void *host, size_t n_amps)
+{
+    if (!c || !host) return fail(QSIM_EINVAL, "NULL argument");
+    if (n_amps != c->n) return fail(QSIM_EINVAL, "n_amps must equal 2^M");
+    int rc = check_device(c);
+    if (rc != QSIM_OK) return rc;
+    QSIM_CUDA(cudaMemcpyAsync(host, c->buf[c->cur], c->amp * c->n, cudaMemcpyDeviceToHost, c->stream),
+              "cudaMemcpy(read state)");
+    QSIM_CUDA(cudaStreamSynchronize(c->stream), "cudaMemcpy(read state)");
+    return QSIM_OK;
+}
+
+int qsim_set_strategy(qsim_ctx *c, int strategy, int tile_bits, int low_bits)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    return plan_options(strategy, tile_bits, low_bits, &c->opts);
+}
+
+int qsim_set_canonicalize(qsim_ctx *c, int enable)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    c->opts.cancel_adjacent = enable != 0;
+    return QSIM_OK;
+}
+
+int qsim_get_plan_stats(qsim_ctx *c, qsim_plan_stats *out)
+{
+    if (!c || !out) return fail(QSIM_EINVAL, "NULL argument");
+    *out = c->stats;
+    return QSIM_OK;
+}
+
+int qsim_synchronize(qsim_ctx *c)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    return check_device(c);
+}
+
+int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    Plan plan;
+    std::string msg;
+    PlanOptions o = c->opts;
+    o.amp_bytes = c->amp;
+    int rc = make_plan(c->M, steps, L, o, &plan, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    fill_stats(plan, c->M, c->amp, &c->stats);
+    if (plan.passes.empty()) return QSIM_OK;
+
+    bool need_scratch = false;
+    for (const Pass &p : plan.passes) need_scratch |= (p.kind == kGather);
+    if (need_scratch) {
+        rc = ensure_scratch(c);
+        if (rc != QSIM_OK) return rc;
+    }
+    // one contiguous table: tile steps | sliced steps | gather tables
+    const size_t off_tile = 0;
+    const size_t sz_tile = plan.tile_steps.size() * sizeof(TileStep);
+    const size_t off_sliced = align_up(off_tile + sz_tile, 256);
+    const size_t sz_sliced = plan.sliced_steps.size() * sizeof(SlicedStep);
+    const size_t off_tab = align_up(off_sliced + sz_sliced, 256);
+    const size_t sz_tab = plan.gather_tables.size() * sizeof(uint64_t);
+    const size_t total = off_tab + sz_tab;
+    if (total > 0) {
+        rc = ensure_plan_buffers(c, total);
+        if (rc != QSIM_OK) return rc;
+        if (sz_tile) std::memcpy(c->h_plan + off_tile, plan.tile_steps.data(), sz_tile);
+        if (sz_sliced) std::memcpy(c->h_plan + off_sliced, plan.sliced_steps.data(), sz_sliced);
+        if (sz_tab) std::memcpy(c->h_plan + off_tab, plan.gather_tables.data(), sz_tab);
+        QSIM_CUDA(cudaMemcpyAsync(c->d_plan, c->h_plan, total, cudaMemcpyHostToDevice, c->stream),
+                  "cudaMemcpy(plan tables)");
+        QSIM_CUDA(cudaEventRecord(c->plan_ev, c->stream), "cudaEventRecord");
+        c->plan_ev_pending = true;
+    }
+    const size_t prof0 = c->prof_kinds.size();  // passes recorded since the last read
+    if (c->profiling) {
+        while (c->ev.size() < 2 * (prof0 + plan.passes.size())) {
+            cudaEvent_t e;
+            QSIM_CUDA(cudaEventCreate(&e), "cudaEventCreate(profiling)");
+            c->ev.push_back(e);
+        }
+    }
+    const TileStep *d_tile = reinterpret_cast<const TileStep *>(c->d_plan + off_tile);
+    const SlicedStep *d_sliced = reinterpret_cast<const SlicedStep *>(c->d_plan + off_sliced);
+    const uint64_t *d_tab = reinterpret_cast<const uint64_t *>(c->d_plan + off_tab);
+    for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
+        const Pass &p = plan.passes[pi];
+        int e = cudaSuccess;
+        if (c->profiling) {
+            QSIM_CUDA(cudaEventRecord(c->ev[2 * (prof0 + pi)], c->stream), "cudaEventRecord");
+            c->prof_kinds.push_back((uint32_t)p.kind);
+            c->prof_bytes.push_back(p.alg_bytes);
+        }
+        if (p.kind == kSweep) {
+            e = launch_sweep(c->buf[c->cur], (int)c->amp, p.sweep, c->d_err, c->stream);
+        } else if (p.kind == kTile) {
+            e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, c->stream);
+        } else {
+            e = launch_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M, p.gather,
+                              d_tab, d_sliced, c->d_err, c->stream);
+            if (e == cudaSuccess) c->cur = 1 - c->cur;
+        }
+        if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "kernel launch");
+        if (c->profiling)
+            QSIM_CUDA(cudaEventRecord(c->ev[2 * (prof0 + pi) + 1], c->stream), "cudaEventRecord");
+    }
+    return QSIM_OK;
+}
+
+int qsim_set_profiling(qsim_ctx *c, int enable)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    c->profiling = enable != 0;
+    c->prof_kinds.clear();
+    c->prof_bytes.clear();
+    return QSIM_OK;
+}
+
+int qsim_get_pass_times(qsim_ctx *c, double *ms, uint32_t *kinds, double *alg_bytes, size_t cap,
+                        size_t *n_out)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    const size_t n = c->prof_kinds.size();
+    if (n_out) *n_out = n;
+    int rc = check_device(c);
+    if (rc != QSIM_OK) return rc;
+    for (size_t i = 0; i < n && i < cap; ++i) {
+        if (ms) {
+            float t = 0.f;
+            QSIM_CUDA(cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]), "cudaEventElapsedTime");
+            ms[i] = t;
+        }
+        if (kinds) kinds[i] = c->prof_kinds[i];
+        if (alg_bytes) alg_bytes[i] = c->prof_bytes[i];
+    }
+    if (cap >= n) {  // everything was read: start a new record
+        c->prof_kinds.clear();
+        c->prof_bytes.clear();
+    }
+    return QSIM_OK;
+}
+
+int qsim_probabilities_device(qsim_ctx *c, double *d_probs, double *norm_out)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    if (reinterpret_cast<uintptr_t>(d_probs) & 7u) return fail(QSIM_EINVAL, "d_probs misaligned");
+    int e = launch_probabilities(c->buf[c->cur], (int)c->amp, c->n, d_probs, c->d_partials,
+                                 probabilities_partials_needed(), c->d_norms, c->stream);
+    if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+    if (norm_out) {
+        int rc = check_device(c);
+        if (rc != QSIM_OK) return rc;
+        QSIM_CUDA(cudaMemcpy(norm_out, c->d_norms, sizeof(double), cudaMemcpyDeviceToHost), "read norm");
+    }
+    return QSIM_OK;
+}
+
+int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_out)
+{
+    if (!c || !host_probs) return fail(QSIM_EINVAL, "NULL argument");
+    if (n != c->n) return fail(QSIM_EINVAL, "n must equal 2^M");
+    int rc = check_device(c);
+    if (rc != QSIM_OK) return rc;
+    const size_t chunk = c->n < kProbChunk ? c->n : kProbChunk;
+    if (!c->d_probs_chunk) QSIM_CUDA(cudaMalloc(&c->d_probs_chunk, sizeof(double) * chunk), "cudaMalloc(probabilities)");
+    const size_t nchunks = (c->n + chunk - 1) / chunk;
+    const char *state = static_cast<const char *>(c->buf[c->cur]);
+    for (size_t k = 0; k < nchunks; ++k) {
+        int e = launch_probabilities(state + k * chunk * c->amp, (int)c->amp, chunk, c->d_probs_chunk,
+                                     c->d_partials, probabilities_partials_needed(), c->d_norms + k,
+                                     c->stream);
+        if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+        QSIM_CUDA(cudaMemcpyAsync(host_probs + k * chunk, c->d_probs_chunk, sizeof(double) * chunk,
+                                  cudaMemcpyDeviceToHost, c->stream),
+                  "cudaMemcpy(probabilities)");
+    }
+    rc = check_device(c);
+    if (rc != QSIM_OK) return rc;
+    if (norm_out) {
+        std::vector<double> norms(nchunks);
+        QSIM_CUDA(cudaMemcpy(norms.data(), c->d_norms, sizeof(double) * nchunks, cudaMemcpyDeviceToHost),
+                  "read norms");
+        // pairwise over chunk sums
+        while (norms.size() > 1) {
+            std::vector<double> nx((norms.size() + 1) / 2);
+            for (size_t i = 0; i < nx.size(); ++i)
+                nx[i] = norms[2 * i] + (2 * i + 1 < norms.size() ? norms[2 * i + 1] : 0.0);
+            norms.swap(nx);
+        }
+        *norm_out = norms[0];
+    }
+    return QSIM_OK;
+}
+
+int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, int strategy,
+                      int tile_bits, int low_bits, int scratch_available, qsim_plan_stats *stats,
+                      uint64_t *order, uint64_t *pass_ends, uint32_t *pass_kinds, size_t cap)
+{
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    PlanOptions o;
+    int rc = plan_options(strategy, tile_bits, low_bits, &o);
+    if (rc != QSIM_OK) return rc;
+    o.amp_bytes = amp;
+    o.scratch_available = scratch_available != 0;
+    Plan plan;
+    std::string msg;
+    rc = make_plan(M, steps, L, o, &plan, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    if (stats) fill_stats(plan, M, amp, stats);
+    if ((order && plan.order.size() > cap) || ((pass_ends || pass_kinds) && plan.passes.size() > cap))
+        return fail(QSIM_EINVAL, "output capacity too small");
+    if (order) std::memcpy(order, plan.order.data(), plan.order.size() * sizeof(uint64_t));
+    if (pass_ends) std::memcpy(pass_ends, plan.pass_ends.data(), plan.pass_ends.size() * sizeof(uint64_t));
+    if (pass_kinds)
+        for (size_t i = 0; i < plan.passes.size(); ++i) pass_kinds[i] = (uint32_t)plan.passes[i].kind;
+    return QSIM_OK;
+}
+
+const char *qsim_last_error(void) { return g_err.c_str(); }
+
+const char *qsim_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// qsim_internal.h -- types shared by the host planner and the CUDA kernels.
+//
+// A circuit is executed as a list of passes over the state.  Each pass is
+// one kernel launch of one of three strategies:
+//   SWEEP  : one step, in place, visiting only the toggled amplitude pairs
+//            (Sec. 2b 'intelligent looping').
+//   TILE   : a run of steps whose targets all lie in a set S of k address
+//            bits; each CTA holds the 2^k amplitudes of one tile (all other
+//            bits fixed) in shared memory, applies the whole run there, and
+//            writes the tile back in place (Sec. 2i: sequential steps
+//            processed together).
+//   GATHER : out-of-place k2(i) = k1(x(i)) with x evaluated per output index
+//            (Sec. 2h product, Sec. 2b final gather); x is an affine map over
+//            GF(2) for CNOT/NOT-only segments, else the step list itself.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+constexpr int kMaxTileBits = 14;      // 2^14 amplitudes per tile at most
+constexpr size_t kMaxTileBytes = 128 * 1024;  // and 128 KiB of shared memory
+constexpr int kMaxHighBits = 10;      // tile bits above the contiguous run
+constexpr int kMaxTileSteps = 256;    // steps per tile pass (shared-memory list)
+constexpr int kMaxGatherSteps = 4096; // steps per general gather pass
+
+// A tile step in the tile's local coordinates.  Local bit q < l is global bit
+// q; local bit l + p is global bit high[p].  cl/pl: control mask/polarity on
+// local bits; tmask: 1 << local target; co/po: control mask/polarity on the
+// bits outside the tile (constant over a tile).
+struct TileStep {
+    uint32_t cl;
+    uint32_t pl;
+    uint32_t tmask;
+    uint32_t pad;
+    uint64_t co;
+    uint64_t po;
+};
+static_assert(sizeof(TileStep) == 32, "TileStep layout");
+
+// A step of a bit-sliced gather pass (16 bytes).  Bit planes are stored as
+// [bit][thread] 32-bit words in shared memory; offsets are byte offsets of a
+// plane for thread 0.
+constexpr int kSlicedThreads = 256;
+constexpr int kSlicedMaxControls = 6;
+struct SlicedStep {
+    uint16_t t_off;    // target plane
+    uint8_t nc;        // number of controls (<= kSlicedMaxControls)
+    uint8_t neg;       // bit q set: control q fires on 0
+    uint16_t c_off[kSlicedMaxControls];
+};
+static_assert(sizeof(SlicedStep) == 16, "SlicedStep layout");
+
+struct SweepParams {
+    uint64_t n_pairs;   // 2^(M-1-c)
+    uint64_t pol;       // control polarity
+    uint64_t half;      // 1 << target
+    uint32_t nins;      // number of zero-bit insertions (controls + target)
+    uint32_t ins[8];    // insertion positions, ascending
+};
+
+struct TilePass {
+    uint32_t k, l, nh;  // tile width, contiguous low bits, high bits
+    uint32_t high[kMaxHighBits];
+    uint64_t n_tiles;   // 2^(M-k)
+    uint32_t step_off;  // offset of this pass's steps in the TileStep buffer
+    uint32_t nsteps;
+    uint32_t all_local; // 1 when no step has a control outside the tile
+    double touched;     // estimated fraction of tiles with an active step
+};
+
+struct GatherPass {
+    uint32_t affine;     // 1: x(i) = A i ^ b through byte tables
+    uint32_t nbytes;     // index bytes covered by tables (affine)
+    uint32_t table_off;  // offset of 256 * nbytes entries in the table buffer
+    uint32_t step_off;   // general: offset in the SlicedStep buffer
+    uint32_t nsteps;     // general: number of steps (applied last to first)
+    uint64_t bvec;       // affine: constant term
+};
+
+enum PassKind : uint32_t { kSweep = 1, kTile = 2, kGather = 3 };
+
+struct Pass {
+    PassKind kind;
+    SweepParams sweep;
+    TilePass tile;
+    GatherPass gather;
+    double alg_bytes;   // bytes read + written as the method requires
+    uint32_t nsteps;    // circuit steps this pass applies
+};
+
+struct PlanOptions {
+    int strategy = QSIM_STRATEGY_AUTO;
+    int tile_bits = 0;  // 0: default for the dtype
+    int low_bits = 0;   // 0: default for the dtype
+    int lookahead = 512;
+    size_t amp_bytes = 16;
+    bool scratch_available = false;
+    bool cancel_adjacent = true;
+};
+
+struct Plan {
+    std::vector<Pass> passes;
+    std::vector<TileStep> tile_steps;
+    std::vector<SlicedStep> sliced_steps;
+    std::vector<uint64_t> gather_tables;
+    std::vector<uint64_t> order;      // circuit step index of each applied step
+    std::vector<uint64_t> pass_ends;  // exclusive end in 'order' of each pass
+    uint64_t steps_in = 0;
+    uint64_t cancelled = 0;
+};
+
+// Host planner (planner.cpp).  Returns QSIM_OK or QSIM_EINVAL with msg set.
+int validate_steps(uint32_t M, const qsim_step *steps, size_t L, std::string *msg);
+int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &opt,
+              Plan *plan, std::string *msg);
+
+// Kernel launchers (kernels.cu).  All return cudaError_t as int.
+int launch_sweep(void *state, int amp_bytes, const SweepParams &p, int *d_err, void *stream);
+int launch_tile(void *state, int amp_bytes, const TilePass &p, const TileStep *d_steps,
+                int *d_err, void *stream);
+int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &p,
+                  const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err, void *stream);
+int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d_probs,
+                         double *d_partials, int n_partials, double *d_norm, void *stream);
+int probabilities_partials_needed();
+size_t tile_smem_bytes(int amp_bytes, int k);
+int num_sms();
+
+}  // namespace qsim

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle.
+
+Amplitudes are only moved, so states must match bit for bit; FP64
+probabilities match the oracle bit for bit too (same two products and one
+sum, no FMA), and the norm within 1e-12 relative (summation order differs).
+Small cases compare every amplitude; the full-size workloads compare sampled
+output rows (the oracle evaluates them one at a time) plus permutation
+invariants of the whole state computed on the device.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_quant_ph_0308158_gb300 import QsimError, Simulator, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NORM_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_quant_ph_0308158_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def run(M, dtype, steps, k1, strategy="auto", tile_bits=0, low_bits=0, buffers="torch"):
+    with Simulator(M, dtype, buffers=buffers) as sim:
+        sim.set_strategy(strategy, tile_bits, low_bits)
+        sim.load_state(k1)
+        sim.apply(steps)
+        out = sim.read_state()
+        stats = sim.plan_stats()
+    return out, stats
+
+
+STRATS = ["auto", "sweep", "tile", "gather", "inplace"]
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("M,L,seed", [(1, 7, 1), (2, 20, 2), (5, 90, 3), (9, 300, 4),
+                                      (12, 333, 5), (14, 260, 6), (17, 200, 7)])
+def test_random_circuits_bit_exact(dtype, strategy, M, L, seed):
+    steps = W.random_circuit(M, L, seed, max_controls=min(8, M - 1))
+    k1 = W.random_state(M, dtype, seed)
+    want = oracle.apply_circuit(M, k1, steps).astype(dtype)
+    got, _ = run(M, dtype, steps, k1, strategy)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("k,l", [(6, 1), (8, 3), (10, 4), (11, 5), (12, 2), (13, 5), (14, 4)])
+def test_tile_geometries(dtype, k, l):
+    M = 18
+    steps = W.mixed_circuit(M, 400, 11)
+    k1 = W.random_state(M, dtype, 11)
+    want = oracle.apply_circuit(M, k1, steps).astype(dtype)
+    if np.dtype(dtype).itemsize * (1 << k) > 128 * 1024:
+        pytest.skip("tile larger than shared memory")
+    got, st = run(M, dtype, steps, k1, "tile", k, l)
+    assert st["tile_passes"] == st["passes"] >= 1
+    np.testing.assert_array_equal(got, want)
+
+
+def test_sec2b_worked_example_on_gpu():
+    M = 3
+    k1 = W.alternating_state(M)
+    steps = W.make_steps([(0, 2, 2)])
+    want = np.array([1, -1, -1, 1, 1, -1, -1, 1]) / math.sqrt(8)
+    for s in STRATS:
+        got, _ = run(M, np.complex128, steps, k1, s)
+        np.testing.assert_array_equal(got, want.astype(np.complex128))
+
+
+@pytest.mark.parametrize("M", [20, 26])
+def test_sec4_parity_program_closed_form_on_gpu(M):
+    k1 = W.alternating_state(M, np.complex64)
+    steps = W.parity_circuit(M)
+    i = np.arange(1 << M, dtype=np.uint64)
+    par = np.zeros_like(i)
+    for b in range(M):
+        par ^= (i >> np.uint64(b)) & np.uint64(1)
+    want = (np.where(par, -1.0, 1.0) / math.sqrt(1 << M)).astype(np.complex64)
+    for s in ("auto", "tile", "gather"):
+        got, _ = run(M, np.complex64, steps, k1, s)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_edge_cases():
+    M = 10
+    k1 = W.random_state(M, np.complex128, 3)
+    # empty circuit
+    got, st = run(M, np.complex128, W.make_steps([]), k1)
+    np.testing.assert_array_equal(got, k1)
+    assert st["passes"] == 0
+    # one NOT on the top bit: contiguous half exchange
+    got, _ = run(M, np.complex128, W.make_steps([(M - 1, 0, 0)]), k1, "sweep")
+    np.testing.assert_array_equal(got, np.concatenate([k1[512:], k1[:512]]))
+    # the maximum number of controls, both polarities
+    full = (1 << M) - 1
+    for pol in (full & ~1, 0b1010101010 & ~1):
+        steps = W.make_steps([(0, full & ~1, pol)])
+        want = oracle.apply_circuit(M, k1, steps)
+        for s in STRATS:
+            got, _ = run(M, np.complex128, steps, k1, s)
+            np.testing.assert_array_equal(got, want)
+    # adjacent equal steps cancel to the identity, and apply when asked to
+    steps = W.make_steps([(3, 1, 1), (3, 1, 1)])
+    got, st = run(M, np.complex128, steps, k1)
+    np.testing.assert_array_equal(got, k1)
+    assert st["steps_cancelled"] == 2
+    with Simulator(M, np.complex128) as sim:
+        sim.set_canonicalize(False)
+        sim.load_state(k1)
+        sim.apply(steps)
+        np.testing.assert_array_equal(sim.read_state(), k1)
+        assert sim.plan_stats()["steps_cancelled"] == 0
+
+
+def test_invalid_circuit_leaves_state_untouched():
+    M = 8
+    k1 = W.random_state(M, np.complex64, 2)
+    with Simulator(M, np.complex64) as sim:
+        sim.load_state(k1)
+        bad = W.make_steps([(0, 2, 2), (1, 2, 2)])
+        with pytest.raises(QsimError) as e:
+            sim.apply(bad)
+        assert e.value.code == -1
+        np.testing.assert_array_equal(sim.read_state(), k1)
+        with pytest.raises(QsimError):
+            sim.load_state(k1[:-1])
+
+
+def test_library_buffers_and_repeated_applies():
+    M = 15
+    steps = W.mixed_circuit(M, 300, 9)
+    k1 = W.random_state(M, np.complex128, 9)
+    want = oracle.apply_circuit(M, oracle.apply_circuit(M, k1, steps), steps)
+    for buffers in ("torch", "library"):
+        with Simulator(M, np.complex128, buffers=buffers) as sim:
+            sim.load_state(k1)
+            sim.apply(steps)
+            sim.apply(steps)
+            np.testing.assert_array_equal(sim.read_state(), want)
+    with Simulator(M, np.complex128, buffers="library", scratch=False) as sim:
+        sim.load_state(k1)
+        sim.apply(steps)
+        assert sim.plan_stats()["gather_passes"] == 0
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("M", [1, 7, 16, 25])
+def test_probabilities_fp64(dtype, M):
+    k1 = W.random_state(M, dtype, M)
+    steps = W.random_circuit(M, 50, M)
+    want_state = oracle.apply_circuit(M, k1, steps)
+    want = oracle.probabilities(want_state)
+    with Simulator(M, dtype) as sim:
+        sim.load_state(k1)
+        sim.apply(steps)
+        p, norm = sim.probabilities(with_norm=True)
+    np.testing.assert_array_equal(p, want)
+    ref = oracle.fsum_pairwise(want)
+    assert abs(norm - ref) <= NORM_RTOL * ref
+    assert abs(norm - 1.0) < 1e-6 if dtype == np.complex64 else abs(norm - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# full-size workloads
+# ----------------------------------------------------------------------------
+
+def _device_hash(t):
+    """Order-independent sums over the state's 64-bit words (wrapping)."""
+    import torch
+    w = t.view(torch.int64)
+    return int(w.sum().item()), int((w * (w | 1)).sum().item())
+
+
+def test_small_cnot_workload_full_state():
+    cfg = W.config_small_cnot()
+    M, steps = cfg["M"], cfg["steps"]
+    for k1 in (W.random_state(M, np.complex128, cfg["state_seed"]), W.alternating_state(M)):
+        want = oracle.apply_circuit(M, k1, steps)
+        for s in STRATS:
+            got, _ = run(M, np.complex128, steps, k1, s)
+            np.testing.assert_array_equal(got, want)
+
+
+def _sampled_check(cfg, strategy, rows=1 << 20):
+    import torch
+    M, dtype, steps = cfg["M"], cfg["dtype"], cfg["steps"]
+    k1 = W.random_state(M, dtype, cfg["state_seed"])
+    rng = np.random.default_rng(12345)
+    r = rng.integers(0, 1 << M, size=rows, dtype=np.uint64)
+    r[:4] = [0, 1, (1 << M) - 2, (1 << M) - 1]
+    src = oracle.source_rows(M, steps, r).astype(np.int64)
+    want = k1[src]
+    with Simulator(M, dtype, scratch=(strategy != "inplace")) as sim:
+        sim.set_strategy(strategy)
+        sim.set_canonicalize(False)
+        sim.load_state(k1)
+        h0 = _device_hash(sim.state_tensor())
+        sim.apply(steps)
+        sim.synchronize()
+        t = sim.state_tensor()
+        got = t[torch.from_numpy(r.astype(np.int64)).cuda()].cpu().numpy()
+        h1 = _device_hash(t)
+        stats = sim.plan_stats()
+    np.testing.assert_array_equal(got, want)
+    assert h0 == h1
+    return stats
+
+
+def test_mixed_m28_workload_sampled():
+    """M=28 complex128, 1000 mixed steps: the benchmarked configuration."""
+    st = _sampled_check(W.config_mixed_m28(), "auto")
+    assert st["gather_passes"] >= 1
+
+
+def test_mixed_m28_workload_inplace_sampled():
+    st = _sampled_check(W.config_mixed_m28(), "inplace")
+    assert st["gather_passes"] == 0
+
+
+def test_adder_m32_workload_sampled():
+    """M=32 complex64 (32 GiB) adder, in place."""
+    st = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 18)
+    assert st["gather_passes"] == 0 and st["passes"] >= 1
