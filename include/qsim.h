@@ -193,6 +193,36 @@ int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, i
                       int tile_bits, int low_bits, int scratch_available, qsim_plan_stats *stats,
                       uint64_t *order, uint64_t *pass_ends, uint32_t *pass_kinds, size_t cap);
 
+/* ---- allocation-free variant (the paper has no counterpart) --------------- */
+
+/* FP64 probabilities and norm of a state held in caller-owned device memory,
+ * computed without a context and without allocating anything.  It serves
+ * callers that cannot allocate device memory when they need the result: a
+ * process whose GPU memory is wholly reserved by another allocator (such as
+ * a framework's caching pool), a plug-in that a host application confines to
+ * a fixed memory budget, or a latency-critical loop that must not enter the
+ * driver's allocator.  (qsim_create allocates, so they cannot use a context.)
+ *   d_state  2^M amplitudes of dtype, aligned to one amplitude; read only
+ *   d_probs  NULL, or 2^M doubles receiving p(i) = re^2 + im^2 (as in
+ *            qsim_probabilities)
+ *   d_norm   one double receiving sum_i p(i)
+ *   stream   cudaStream_t (NULL = legacy default stream); the work is queued
+ *            there and the call returns without waiting
+ * Scratch: the norm's per-block partial sums live in a fixed device array of
+ * 1024 doubles (8 KiB) compiled into the library; every GPU that loads the
+ * library holds it until the process exits.  The launch never uses more
+ * than 1024 blocks, so every M in [1, QSIM_MAX_QUBITS] fits; M outside that
+ * range, an unknown dtype, a NULL d_state/d_norm or a misaligned pointer
+ * returns QSIM_EINVAL with a message in qsim_last_error().  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture on the
+ * device.  All calls share the one array and every call overwrites it, so
+ * calls whose work overlaps on the GPU (different streams, or several host
+ * threads) race: serialise them.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
+int qsim_probabilities_noalloc(const void *d_state, uint32_t M, int dtype, double *d_probs,
+                               double *d_norm, void *stream);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 
 /* Message describing the last error on this host thread ("" if none). */

@@ -43,6 +43,7 @@ EXPORTS = (
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
+    "qsim_probabilities_noalloc",
 )
 
 
@@ -99,6 +100,7 @@ def load() -> ctypes.CDLL:
             "qsim_probabilities": ([p, p, sz, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_probabilities_device": ([p, p, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_plan_circuit": ([u32, i, p, sz, i, i, i, i, ctypes.POINTER(PlanStats), p, p, p, sz], i),
+            "qsim_probabilities_noalloc": ([p, u32, i, p, p, p], i),
             "qsim_last_error": ([], ctypes.c_char_p),
             "qsim_version": ([], ctypes.c_char_p),
         }

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wextra", "-Wno-unused-parameter"]
 
-SOURCES = ["kernels.cu", "qsim_api.cu", "planner.cpp"]
+SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "planner.cpp"]
 HEADERS = [os.path.join(CSRC, "qsim_internal.h"), os.path.join(ROOT, "include", "qsim.h")]
 
 

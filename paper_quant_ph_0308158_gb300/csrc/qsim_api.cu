@@ -40,6 +40,8 @@ constexpr size_t kProbChunk = size_t(1) << 24;  // amplitudes per host-probabili
 
 }  // namespace
 
+void qsim::set_last_error(const std::string &msg) { g_err = msg; }
+
 struct qsim_ctx {
     uint32_t M = 0;
     int dtype = 0;

@@ -119,6 +119,9 @@ int validate_steps(uint32_t M, const qsim_step *steps, size_t L, std::string *ms
 int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &opt,
               Plan *plan, std::string *msg);
 
+// Message returned by qsim_last_error() on this host thread (qsim_api.cu).
+void set_last_error(const std::string &msg);
+
 // Kernel launchers (kernels.cu).  All return cudaError_t as int.
 int launch_sweep(void *state, int amp_bytes, const SweepParams &p, int *d_err, void *stream);
 int launch_tile(void *state, int amp_bytes, const TilePass &p, const TileStep *d_steps,
