@@ -62,12 +62,18 @@ def workload(name: str):
         return W.config_adder_m32()
     if name == "cnot_m16":
         return W.config_small_cnot()
+    if name == "mixed_m24":  # 256 MiB: the small case for ncu captures
+        return W.config_mixed(24)
+    if name == "cnot_m28":  # CNOT-only: one affine gather pass
+        return W.config_cnot(28)
+    if name == "adder_m28":  # 2 GiB in-place adder: the small case for tile-kernel captures
+        return W.config_adder(13)
     raise SystemExit("unknown workload " + name)
 
 
 def strategy_for(name: str) -> str:
     # the adder workload is specified in place
-    return "inplace" if name == "adder_m32" else "auto"
+    return "inplace" if name.startswith("adder") else "auto"
 
 
 # ----------------------------------------------------------------------------
@@ -125,7 +131,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -176,7 +182,7 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel_kind: str, wl: str):
+def ncu_traffic(kernel: str, wl: str):
     """DRAM bytes per launch recorded from an ncu capture of the current kernel
     source (profiles/traffic.json), scaled to the benchmarked launch; None if
     absent or taken on a different kernel source."""
@@ -186,7 +192,7 @@ def ncu_traffic(kernel_kind: str, wl: str):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    e = rec.get(wl, {}).get(kernel_kind)
+    e = rec.get(wl, {}).get(kernel)
     if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return float(e["dram_bytes_per_launch"])
@@ -269,6 +275,11 @@ def run_ours(args, rank, ws, local):
     sim = Simulator(M, dtype, scratch=(strategy != "inplace"))
     sim.set_strategy(strategy)
     sim.set_canonicalize(False)
+    jit_ms = None
+    if args.jit and strategy != "inplace":
+        from paper_quant_ph_0308158_gb300 import jit_precompile
+        jit_ms = jit_precompile(M, dtype, steps, canonicalize=False)
+        sim.set_jit(True)
     probs = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -312,14 +323,12 @@ def run_ours(args, rank, ws, local):
         a[1] += ms
         a[2] += by
     dom = max(by_kind.items(), key=lambda kv: kv[1][1])
-    dkind, (dlaunch, dms, dbytes) = dom
+    dkernel, (dlaunch, dms, dbytes) = dom
     peak, peak_src = hbm_peak()
     achieved = (dbytes / dlaunch) / (dms / dlaunch * 1e-3) / 1e9
-    traffic = ncu_traffic(dkind, cfg["name"])
+    traffic = ncu_traffic(dkernel, cfg["name"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": {"gather": "gather_sliced_kernel" if L > 0 else "gather",
-                           "tile": "tile_kernel", "sweep": "sweep_kernel"}[dkind],
+                "frac": achieved / peak, "traffic": traffic, "kernel": dkernel,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6800 GB/s",
                 "algorithmic_bytes_per_launch": dbytes / dlaunch,
@@ -381,7 +390,10 @@ def run_ours(args, rank, ws, local):
                        "sweep_passes": stats["sweep_passes"],
                        "steps_cancelled": stats["steps_cancelled"],
                        "full_pass_equiv": stats["full_pass_equiv"],
-                       "step_includes": "plan + all passes + FP64 probabilities"},
+                       "step_includes": "plan + all passes + FP64 probabilities",
+                       "jit": bool(jit_ms is not None),
+                       "jit_compile_ms": jit_ms,
+                       "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in by_kind.items()}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -393,16 +405,93 @@ def run_ours(args, rank, ws, local):
     return 0
 
 
+def run_batch(args, rank, ws, local):
+    """Batched circuits: one captured graph of persistent launches per run,
+    against one plain launch per circuit pass (same plans, same states)."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Batch, build
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    build.build()
+    torch.cuda.set_device(local)
+    mix = "mixed" if args.workload.endswith("mixed") else "cnot"
+    n = args.batch_size
+    specs = W.batch_specs(n, seed=4, mix=mix)
+    dtype = np.dtype(np.complex64)
+    t0 = time.perf_counter()
+    b = Batch([(s["M"], s["steps"]) for s in specs], dtype)
+    create_s = time.perf_counter() - t0
+    for i, sp in enumerate(specs):
+        b.load_state(i, W.random_state(sp["M"], dtype, sp["state_seed"]))
+    info = b.info()
+    stream = torch.cuda.ExternalStream(info["stream"])
+    amp_steps = info["amplitude_steps"]
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        b.synchronize()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        b.synchronize()
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), ws) / k
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_batch = timed(b.run, args.steps)
+    clk = clocks.stop()
+    ms_plain = timed(b.run_plain, max(1, args.steps // 4))
+    peak, peak_src = hbm_peak()
+    achieved = info["algorithmic_bytes"] / (ms_batch * 1e-3) / 1e9
+    value = ws * amp_steps / (ms_batch * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic (seeded random states and circuits)",
+            "config": {"workload": "batch%d_%s" % (n, mix), "circuits": n, "M_range": [10, 22],
+                       "L_range": [50, 2000], "levels": info["levels"], "items": info["items"],
+                       "arena_bytes": info["arena_bytes"], "create_s": create_s,
+                       "plain_ms_per_run": ms_plain,
+                       "plain_value": ws * amp_steps / (ms_plain * 1e-3),
+                       "batched_over_plain": ms_plain / ms_batch,
+                       "step": "one run of every circuit (graph replay)",
+                       "l2": "inputs larger than L2 (%.1f GB of states)" % (info["arena_bytes"] / 2e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel",
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": info["algorithmic_bytes"] / max(1, info["levels"]),
+                         "avg_launch_ms": ms_batch / max(1, info["levels"])},
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": args.steps * info["levels"],
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "cnot_m16"])
+    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28",
+                             "batch_cnot", "batch_mixed"])
+    ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
     ap.add_argument("--ref-steps-per-step", type=int, default=2,
                     help="oracle steps per timed reference step")
+    ap.add_argument("--no-jit", dest="jit", action="store_false",
+                    help="use the general bit-sliced gather instead of compiled kernels")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -411,6 +500,8 @@ def main():
     rank, ws, local = dist_init()
     if args.impl == "reference":
         rc = run_reference(args, rank, ws)
+    elif args.workload.startswith("batch"):
+        rc = run_batch(args, rank, ws, local)
     else:
         rc = run_ours(args, rank, ws, local)
     if ws > 1:

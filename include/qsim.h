@@ -142,6 +142,24 @@ int qsim_apply_circuit(qsim_ctx *ctx, const qsim_step *steps, size_t L);
  * of them are the lowest address bits (0 = default). */
 int qsim_set_strategy(qsim_ctx *ctx, int strategy, int tile_bits, int low_bits);
 
+/* Circuit-specialised gather kernels.  With enable = 1, every out-of-place
+ * gather segment of at least 32 steps that is not a plain NOT/CNOT run (those
+ * use GF(2) tables) is written out as CUDA source -- one bit-plane update per
+ * step, the steps last to first -- and compiled for the GPU by NVRTC on first
+ * use; the compiled kernel is cached for the life of the process, keyed by
+ * (M, dtype, steps), and reused by every later apply of the same segment.
+ * The first apply of a new circuit pays the compile time (about a second);
+ * the general bit-sliced kernel runs when enable = 0 (the default).  Returns
+ * QSIM_ECUDA from qsim_apply_circuit if NVRTC is not available. */
+int qsim_set_jit(qsim_ctx *ctx, int enable);
+
+/* Compile, without a GPU, the kernels that qsim_apply_circuit with jit on
+ * would compile for this circuit (strategy GATHER), so that a later apply
+ * finds them cached.  canonicalize as for qsim_set_canonicalize.
+ * compile_ms (may be NULL) receives the compile time spent by this call. */
+int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L, int canonicalize,
+                        double *compile_ms);
+
 /* Adjacent equal steps cancel in pairs (each step is its own inverse,
  * Sec. 2a).  enable = 1 (default) removes them before planning; 0 applies
  * every step as given. */
@@ -154,9 +172,10 @@ int qsim_get_plan_stats(qsim_ctx *ctx, qsim_plan_stats *out);
  * qsim_apply_circuit is bracketed by CUDA events on the context's stream, and
  * the records accumulate over successive applies.  qsim_get_pass_times waits
  * for queued work and writes, for each recorded pass (at most cap), the
- * device time in milliseconds, the pass kind (1 sweep, 2 tile, 3 gather) and
- * its algorithmic bytes (any pointer may be NULL); *n_out receives the number
- * of recorded passes.  When cap covers them all the record is cleared. */
+ * device time in milliseconds, the kernel (1 sweep, 2 tile, 3 affine gather,
+ * 4 bit-sliced gather, 5 compiled gather) and its algorithmic bytes (any
+ * pointer may be NULL); *n_out receives the number of recorded passes.  When
+ * cap covers them all the record is cleared. */
 int qsim_set_profiling(qsim_ctx *ctx, int enable);
 int qsim_get_pass_times(qsim_ctx *ctx, double *ms, uint32_t *kinds, double *alg_bytes,
                         size_t cap, size_t *n_out);
@@ -176,6 +195,56 @@ int qsim_probabilities(qsim_ctx *ctx, double *host_probs, size_t n, double *norm
  * aligned), queued on the context's stream.  norm_out (may be NULL) is a
  * host pointer; when given the call waits for the result. */
 int qsim_probabilities_device(qsim_ctx *ctx, double *d_probs, double *norm_out);
+
+/* ---- batches of independent circuits --------------------------------------- */
+
+/* A batch runs n independent wiring diagrams, circuit i on its own
+ * 2^M[i]-amplitude state, all of one dtype.  Not in the paper, which runs one
+ * circuit at a time: many small circuits each leave most of the GPU idle
+ * and pay a launch per pass, so a batch plans every circuit once (out-of-place
+ * gather passes: GF(2) tables for NOT/CNOT runs, bit-sliced evaluation
+ * otherwise, sweeps for steps with more than eight controls), groups the
+ * p-th pass of every circuit into one persistent launch (level p), captures
+ * the levels of a run into a CUDA graph and replays it.  Every step is
+ * applied (no cancellation). */
+typedef struct qsim_batch qsim_batch;
+
+typedef struct qsim_batch_stats {
+    uint64_t circuits;
+    uint64_t levels;          /* persistent launches per run                 */
+    uint64_t items;           /* work items per run (16384 outputs each)     */
+    uint64_t passes;          /* circuit passes per run                      */
+    uint64_t amplitude_steps; /* sum over circuits of 2^M[i] * L[i]          */
+    double algorithmic_bytes; /* bytes read + written per run                */
+    uint64_t arena_bytes;     /* device memory of the two state arenas       */
+    void *stream;             /* cudaStream_t the batch runs on              */
+} qsim_batch_stats;
+
+/* Plan and allocate a batch.  M[i] in [1, QSIM_MAX_QUBITS]; steps[i] points to
+ * L[i] steps (copied).  The states start zero-filled.  Device memory: two
+ * arenas of sum_i 2^M[i] amplitudes.  QSIM_EINVAL names the first invalid
+ * circuit; QSIM_ENOMEM when the arenas do not fit. */
+int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *const *steps,
+                      const size_t *L, qsim_batch **out);
+void qsim_batch_destroy(qsim_batch *b);
+
+/* Copy circuit i's state in from / out to host memory (n_amps = 2^M[i]);
+ * synchronous. */
+int qsim_batch_load_state(qsim_batch *b, size_t i, const void *host_amps, size_t n_amps);
+int qsim_batch_read_state(qsim_batch *b, size_t i, void *host_amps, size_t n_amps);
+
+/* Device pointer of circuit i's current state. */
+void *qsim_batch_state_device(qsim_batch *b, size_t i);
+
+/* Apply every circuit once: one graph launch (asynchronous). */
+int qsim_batch_run(qsim_batch *b);
+
+/* Apply every circuit once with one plain kernel launch per circuit pass,
+ * no graph (the comparison for qsim_batch_run; same kernels' arithmetic). */
+int qsim_batch_run_plain(qsim_batch *b);
+
+int qsim_batch_synchronize(qsim_batch *b);
+int qsim_batch_info(qsim_batch *b, qsim_batch_stats *out);
 
 /* ---- host-only planning (no GPU needed) ------------------------------------ */
 

@@ -33,6 +33,8 @@ QSIM_C128 = 1
 
 STRATEGY = {"auto": 0, "sweep": 1, "tile": 2, "gather": 3, "inplace": 4}
 PASS_KIND = {1: "sweep", 2: "tile", 3: "gather"}
+KERNEL = {1: "sweep_kernel", 2: "tile_kernel", 3: "gather_affine_kernel",
+          4: "gather_sliced_kernel", 5: "qsim_jit_gather"}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libqsim.so")
 
@@ -40,10 +42,13 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 EXPORTS = (
     "qsim_create", "qsim_create_with_buffers", "qsim_destroy", "qsim_load_state",
     "qsim_read_state", "qsim_state_device", "qsim_apply_circuit", "qsim_set_strategy",
-    "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times",
+    "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
+    "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
-    "qsim_probabilities_noalloc",
+    "qsim_probabilities_noalloc", "qsim_batch_create", "qsim_batch_destroy",
+    "qsim_batch_load_state", "qsim_batch_read_state", "qsim_batch_state_device", "qsim_batch_run",
+    "qsim_batch_run_plain", "qsim_batch_synchronize", "qsim_batch_info",
 )
 
 
@@ -58,6 +63,16 @@ class PlanStats(ctypes.Structure):
                 ("passes", ctypes.c_uint64), ("sweep_passes", ctypes.c_uint64),
                 ("tile_passes", ctypes.c_uint64), ("gather_passes", ctypes.c_uint64),
                 ("algorithmic_bytes", ctypes.c_double), ("full_pass_equiv", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("circuits", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("items", ctypes.c_uint64), ("passes", ctypes.c_uint64),
+                ("amplitude_steps", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_double),
+                ("arena_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +109,8 @@ def load() -> ctypes.CDLL:
             "qsim_set_strategy": ([p, i, i, i], i),
             "qsim_set_canonicalize": ([p, i], i),
             "qsim_set_profiling": ([p, i], i),
+            "qsim_set_jit": ([p, i], i),
+            "qsim_jit_precompile": ([u32, i, p, sz, i, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_get_pass_times": ([p, p, p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_get_plan_stats": ([p, ctypes.POINTER(PlanStats)], i),
             "qsim_synchronize": ([p], i),
@@ -101,6 +118,15 @@ def load() -> ctypes.CDLL:
             "qsim_probabilities_device": ([p, p, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_plan_circuit": ([u32, i, p, sz, i, i, i, i, ctypes.POINTER(PlanStats), p, p, p, sz], i),
             "qsim_probabilities_noalloc": ([p, u32, i, p, p, p], i),
+            "qsim_batch_create": ([sz, p, i, p, p, pp], i),
+            "qsim_batch_destroy": ([p], None),
+            "qsim_batch_load_state": ([p, sz, p, sz], i),
+            "qsim_batch_read_state": ([p, sz, p, sz], i),
+            "qsim_batch_state_device": ([p, sz], p),
+            "qsim_batch_run": ([p], i),
+            "qsim_batch_run_plain": ([p], i),
+            "qsim_batch_synchronize": ([p], i),
+            "qsim_batch_info": ([p, ctypes.POINTER(BatchStats)], i),
             "qsim_last_error": ([], ctypes.c_char_p),
             "qsim_version": ([], ctypes.c_char_p),
         }
@@ -241,6 +267,9 @@ class Simulator:
     def set_strategy(self, strategy: str = "auto", tile_bits: int = 0, low_bits: int = 0):
         _check(self._lib.qsim_set_strategy(self._ctx, STRATEGY[strategy], tile_bits, low_bits))
 
+    def set_jit(self, enable: bool):
+        _check(self._lib.qsim_set_jit(self._ctx, int(bool(enable))))
+
     def set_canonicalize(self, enable: bool):
         _check(self._lib.qsim_set_canonicalize(self._ctx, int(bool(enable))))
 
@@ -252,7 +281,7 @@ class Simulator:
         _check(self._lib.qsim_set_profiling(self._ctx, int(bool(enable))))
 
     def pass_times(self):
-        """[(kind, ms, algorithmic bytes)] for every pass recorded since the
+        """[(kernel, ms, algorithmic bytes)] for every pass recorded since the
         last call (profiling must be on); clears the record."""
         n = ctypes.c_size_t(0)
         _check(self._lib.qsim_get_pass_times(self._ctx, None, None, None, 0, ctypes.byref(n)))
@@ -262,7 +291,7 @@ class Simulator:
         by = np.zeros(max(k, 1), np.float64)
         _check(self._lib.qsim_get_pass_times(self._ctx, _ptr(ms), _ptr(kinds), _ptr(by), k,
                                              ctypes.byref(n)))
-        return [(PASS_KIND[int(kinds[i])], float(ms[i]), float(by[i])) for i in range(k)]
+        return [(KERNEL[int(kinds[i])], float(ms[i]), float(by[i])) for i in range(k)]
 
     def plan_stats(self) -> dict:
         st = PlanStats()
@@ -290,6 +319,78 @@ class Simulator:
         _check(self._lib.qsim_probabilities_device(self._ctx, ctypes.c_void_p(out_ptr),
                                                    ctypes.byref(norm) if with_norm else None))
         return norm.value if with_norm else None
+
+
+def jit_precompile(M: int, dtype, steps, canonicalize: bool = True) -> float:
+    """Compile the circuit-specialised kernels of a circuit; returns compile ms."""
+    s = as_steps(steps)
+    ms = ctypes.c_double(0.0)
+    _check(load().qsim_jit_precompile(M, dtype_code(dtype), _ptr(s), len(s), int(canonicalize),
+                                      ctypes.byref(ms)))
+    return ms.value
+
+
+class Batch:
+    """Independent circuits run together: ``run()`` replays one captured graph
+    of persistent launches; ``run_plain()`` launches one kernel per circuit
+    pass.  circuits: list of (M, steps)."""
+
+    def __init__(self, circuits, dtype=np.complex64):
+        self._lib = load()
+        self.dtype = np.dtype(dtype)
+        self.M = [int(m) for m, _ in circuits]
+        self._steps = [as_steps(s) for _, s in circuits]
+        n = len(circuits)
+        Ms = (ctypes.c_uint32 * n)(*self.M)
+        ptrs = (ctypes.c_void_p * n)(*[s.ctypes.data if len(s) else 0 for s in self._steps])
+        Ls = (ctypes.c_size_t * n)(*[len(s) for s in self._steps])
+        self._b = ctypes.c_void_p()
+        _check(self._lib.qsim_batch_create(n, ctypes.cast(Ms, ctypes.c_void_p), dtype_code(self.dtype),
+                                           ctypes.cast(ptrs, ctypes.c_void_p),
+                                           ctypes.cast(Ls, ctypes.c_void_p), ctypes.byref(self._b)))
+
+    def close(self):
+        if self._b:
+            self._lib.qsim_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_state(self, i: int, k: np.ndarray):
+        a = np.ascontiguousarray(k, dtype=self.dtype)
+        _check(self._lib.qsim_batch_load_state(self._b, i, _ptr(a), a.shape[0]))
+
+    def read_state(self, i: int) -> np.ndarray:
+        out = np.empty(1 << self.M[i], dtype=self.dtype)
+        _check(self._lib.qsim_batch_read_state(self._b, i, _ptr(out), out.shape[0]))
+        return out
+
+    def state_ptr(self, i: int) -> int:
+        return int(self._lib.qsim_batch_state_device(self._b, i) or 0)
+
+    def run(self):
+        _check(self._lib.qsim_batch_run(self._b))
+
+    def run_plain(self):
+        _check(self._lib.qsim_batch_run_plain(self._b))
+
+    def synchronize(self):
+        _check(self._lib.qsim_batch_synchronize(self._b))
+
+    def info(self) -> dict:
+        st = BatchStats()
+        _check(self._lib.qsim_batch_info(self._b, ctypes.byref(st)))
+        return st.as_dict()
 
 
 def version() -> str:

@@ -11,7 +11,7 @@
 //                         (Sec. 2i: sequential steps processed together).
 //   gather_affine_kernel  k2(i) = k1(A i ^ b) for CNOT/NOT segments
 //                         (Sec. 2h product of the steps, Sec. 2b gather).
-//   gather_sliced_kernel  k2(i) = k1(x(i)) with x(i) evaluated for 32 output
+//   gather_sliced_kernel  k2(i) = k1(x(i)) with x(i) evaluated for 64 output
 //                         indices at once in bit-sliced form, steps applied
 //                         last to first (Sec. 2h product, Sec. 2b gather).
 //   probs_kernel          p(i) = re^2 + im^2 in FP64 and a norm partial sum.
@@ -121,86 +121,98 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(char *__restrict__ stat
 //     in-place stores
 // ============================================================================
 
+// Per tile, the permutation of its 2^k local indices depends only on which
+// steps are active there (their controls outside the tile are constant over
+// a tile).  It is kept as a table perm[j] = source of local output j and is
+// recomputed only when the set of active steps changes from one tile to the
+// next.  Tiles are dealt to CTAs in contiguous ranges of the tile id, whose
+// highest bits are the out-of-tile control bits, so a CTA sees long runs of
+// tiles with the same active set.
+constexpr int kTileThreads = 512;
+constexpr int kMaxOutBits = 40;
+constexpr int kMaskWords = kMaxTileSteps / 32;
+
 struct TileKParams {
     char *state;
     const TileStep *steps;
     int *err;
     uint64_t n_tiles;
-    uint32_t k, l, nh, nsteps, all_local, stages;
+    uint32_t k, l, nh, nsteps, all_local, stages, nout;
     uint32_t high[kMaxHighBits];
+    uint32_t outpos[kMaxOutBits];  // global bit of tile-id bit q
 };
 
 struct TileStageMeta {
-    uint64_t base;  // global index of local index 0; ~0 = no tile
-    int32_t cnt;    // active steps
-    int32_t pad;
+    uint64_t base;                 // global index of local index 0; ~0 = no tile
+    uint32_t mask[kMaskWords];     // active steps
+    uint32_t same;                 // active set equals the previous tile's
+    uint32_t pad;
 };
 
 constexpr uint64_t kNoTile = ~0ull;
 
-__device__ __forceinline__ uint64_t tile_base(uint64_t tile, const TileKParams &p)
+__device__ __forceinline__ uint64_t tile_base(uint64_t tile, const uint32_t *outpos)
 {
-    uint64_t b = tile << p.l;
-    for (uint32_t q = 0; q < p.nh; ++q) b = insert_zero(b, p.high[q]);
+    uint64_t b = 0;
+    for (uint32_t q = 0; tile; ++q, tile >>= 1)
+        if (tile & 1ull) b |= 1ull << outpos[q];
     return b;
 }
 
-// Warp 0: pick this CTA's next tile that has an active step, record its
-// active steps (in order), arm the stage barrier and issue one bulk copy per
-// contiguous run of 2^l amplitudes.
+// Warp 0: find this CTA's next tile with an active step, record the active
+// set, arm the stage barrier and issue one bulk copy per contiguous run of
+// 2^l amplitudes.
 template <int B>
-__device__ uint64_t tile_produce(const TileKParams &p, int s, uint64_t next, char *buf,
-                                 const uint64_t *depo, TileStageMeta *meta, uint2 *list,
-                                 const TileStep *steps_sm, uint64_t *bar)
+__device__ uint64_t tile_produce(const TileKParams &p, int s, uint64_t next, uint64_t end,
+                                 char *buf, const uint64_t *depo, TileStageMeta *meta,
+                                 const TileStep *steps_sm, const uint32_t *outpos, uint64_t *bar,
+                                 uint32_t (&last)[kMaskWords], bool &have_last)
 {
     const int lane = threadIdx.x & 31;
     uint64_t base = kNoTile;
-    int cnt = 0;
-    while (next < p.n_tiles) {
-        base = tile_base(next, p);
-        next += gridDim.x;
-        if (p.all_local) {
-            cnt = (int)p.nsteps;
-            break;
-        }
-        cnt = 0;
-        for (uint32_t s0 = 0; s0 < p.nsteps; s0 += 32) {
-            const uint32_t i = s0 + lane;
+    uint32_t mask[kMaskWords];
+    bool any = false;
+    while (next < end) {
+        base = tile_base(next, outpos);
+        ++next;
+        any = false;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) {
+            const uint32_t i = w * 32 + lane;
             bool act = false;
-            TileStep st;
-            if (i < p.nsteps) {
-                st = steps_sm[i];
-                act = (base & st.co) == st.po;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, act);
-            if (act) {
-                const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                list[pos] = make_uint2(st.cl | (st.pl << 16), st.tmask);
-            }
-            cnt += __popc(bal);
+            if (i < p.nsteps) act = p.all_local || (base & steps_sm[i].co) == steps_sm[i].po;
+            mask[w] = __ballot_sync(0xffffffffu, act);
+            any |= mask[w] != 0;
         }
-        if (cnt > 0) break;
+        if (any) break;
         base = kNoTile;
     }
+    bool same = have_last;
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) same = same && (mask[w] == last[w]);
     if (lane == 0) {
         meta[s].base = base;
-        meta[s].cnt = cnt;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) meta[s].mask[w] = mask[w];
+        meta[s].same = same ? 1u : 0u;
     }
     if (base == kNoTile) return next;
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) last[w] = mask[w];
+    have_last = true;
     fence_proxy_async_smem();
     const uint32_t run_bytes = (uint32_t)B << p.l;
     if (lane == 0) mbar_arrive_expect_tx(bar, run_bytes << p.nh);
     __syncwarp();
-    const char *g = p.state;
     for (uint32_t r = lane; r < (1u << p.nh); r += 32) {
         const uint64_t gi = base + depo[r];
-        bulk_g2s(buf + (size_t)r * run_bytes, g + gi * B, run_bytes, bar);
+        bulk_g2s(buf + (size_t)r * run_bytes, p.state + gi * B, run_bytes, bar);
     }
     return next;
 }
 
 template <int B>
-__global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileKParams p)
+__global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(TileKParams p)
 {
     using A = typename AmpOf<B>::T;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -211,75 +223,89 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileKParams p)
     TileStageMeta *meta = reinterpret_cast<TileStageMeta *>(depo + (1u << p.nh));
     uint64_t *bars = reinterpret_cast<uint64_t *>(meta + p.stages);
     TileStep *steps_sm = reinterpret_cast<TileStep *>(bars + p.stages);
-    uint2 *lists = reinterpret_cast<uint2 *>(steps_sm + p.nsteps);  // stages (+1) lists
+    uint32_t *outpos = reinterpret_cast<uint32_t *>(steps_sm + p.nsteps);
+    uint16_t *perm = reinterpret_cast<uint16_t *>(outpos + kMaxOutBits);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    for (uint32_t r = tid; r < (1u << p.nh); r += kThreads) {
+    for (uint32_t r = tid; r < (1u << p.nh); r += kTileThreads) {
         uint64_t d = 0;
         for (uint32_t q = 0; q < p.nh; ++q) d |= (uint64_t)((r >> q) & 1u) << p.high[q];
         depo[r] = d;
     }
-    for (uint32_t i = tid; i < p.nsteps; i += kThreads) steps_sm[i] = p.steps[i];
+    for (uint32_t i = tid; i < p.nsteps; i += kTileThreads) steps_sm[i] = p.steps[i];
+    for (uint32_t i = tid; i < kMaxOutBits; i += kTileThreads) outpos[i] = p.outpos[i];
     if (tid == 0) {
         for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint2 *shared_list = lists + (size_t)p.stages * kMaxTileSteps;
-    if (p.all_local) {
-        for (uint32_t i = tid; i < p.nsteps; i += kThreads)
-            shared_list[i] = make_uint2(steps_sm[i].cl | (steps_sm[i].pl << 16), steps_sm[i].tmask);
-    }
-    uint64_t next = blockIdx.x;
+
+    // contiguous range of tile ids for this CTA
+    const uint64_t per = (p.n_tiles + gridDim.x - 1) / gridDim.x;
+    uint64_t next = (uint64_t)blockIdx.x * per;
+    const uint64_t end = next + per < p.n_tiles ? next + per : p.n_tiles;
+    uint32_t last[kMaskWords];
+    bool have_last = false;
     if (warp == 0) {
         for (uint32_t s = 0; s < p.stages; ++s)
-            next = tile_produce<B>(p, (int)s, next, bufs + tile_bytes * s, depo, meta,
-                                   lists + (size_t)s * kMaxTileSteps, steps_sm, &bars[s]);
+            next = tile_produce<B>(p, (int)s, next, end, bufs + tile_bytes * s, depo, meta, steps_sm,
+                                   outpos, &bars[s], last, have_last);
     }
     __syncthreads();
 
     const uint32_t lmask = (1u << p.l) - 1u;
     uint32_t parity = 0;  // bit s: phase of stage s
+    A *st = reinterpret_cast<A *>(p.state);
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
+        if (!meta[s].same) {
+            // new active set: rebuild perm (steps last to first on each index)
+            for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 8) {
+                uint32_t src[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) src[e] = j0 + tid + e * kTileThreads;
+                for (int q = (int)p.nsteps - 1; q >= 0; --q) {
+                    if (!((meta[s].mask[q >> 5] >> (q & 31)) & 1u)) continue;
+                    const uint32_t cl = steps_sm[q].cl, pl = steps_sm[q].pl, tm = steps_sm[q].tmask;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if ((src[e] & cl) == pl) src[e] ^= tm;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t j = j0 + tid + e * kTileThreads;
+                    if (j < tile_amps) perm[j] = (uint16_t)src[e];
+                }
+            }
+        }
         bool ok = false;
         for (unsigned w = 0; w < kWaitLimit && !ok; ++w) ok = mbar_try_wait(&bars[s], (parity >> s) & 1u);
-        if (__syncthreads_or(!ok)) {
+        if (__syncthreads_or(!ok)) {  // also publishes perm
             if (tid == 0) atomicOr(p.err, 1);
             return;
         }
         parity ^= 1u << s;
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
-        const uint2 *list = p.all_local ? shared_list : lists + (size_t)s * kMaxTileSteps;
-        const int cnt = meta[s].cnt;
-        A *st = reinterpret_cast<A *>(p.state);
-        for (uint32_t j0 = 0; j0 < tile_amps; j0 += kThreads * 8) {
-            uint32_t src[8];
+        for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 4) {
+            A v[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) src[e] = j0 + tid + e * kThreads;
-            for (int q = cnt - 1; q >= 0; --q) {
-                const uint2 d = list[q];
-                const uint32_t cl = d.x & 0xffffu, pl = d.x >> 16, tm = d.y;
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if ((src[e] & cl) == pl) src[e] ^= tm;
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t j = j0 + tid + e * kTileThreads;
+                if (j < tile_amps) v[e] = buf[perm[j]];
             }
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint32_t j = j0 + tid + e * kThreads;
-                if (j < tile_amps) {
-                    const A v = buf[src[e]];
-                    st[base + depo[j >> p.l] + (j & lmask)] = v;
-                }
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t j = j0 + tid + e * kTileThreads;
+                if (j < tile_amps) st[base + depo[j >> p.l] + (j & lmask)] = v[e];
             }
         }
         __syncthreads();
         if (warp == 0)
-            next = tile_produce<B>(p, (int)s, next, bufs + tile_bytes * s, depo, meta,
-                                   lists + (size_t)s * kMaxTileSteps, steps_sm, &bars[s]);
+            next = tile_produce<B>(p, (int)s, next, end, bufs + tile_bytes * s, depo, meta, steps_sm,
+                                   outpos, &bars[s], last, have_last);
         __syncthreads();
     }
 }
@@ -288,28 +314,24 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileKParams p)
 // (c) gather passes
 // ============================================================================
 
-template <int B, bool WIDE>
-__global__ void __launch_bounds__(kThreads) gather_affine_kernel(const char *__restrict__ in,
-                                                                 char *__restrict__ out, uint64_t n,
-                                                                 const uint64_t *__restrict__ tables,
-                                                                 uint32_t nbytes, uint64_t bvec)
+// Affine gather of outputs [o0, o1): x(i) = b ^ XOR over index bytes of
+// per-byte tables (already in shared memory).
+template <int B, bool WIDE, typename I>
+__device__ __forceinline__ void affine_range(const char *__restrict__ in, char *__restrict__ out,
+                                             uint64_t o0, uint64_t o1, uint64_t step,
+                                             const I *tab, uint32_t nbytes, uint64_t bvec)
 {
     using A = typename AmpOf<B>::T;
-    using I = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
-    __shared__ I tab[5 * 256];
-    for (uint32_t i = threadIdx.x; i < nbytes * 256; i += kThreads) tab[i] = (I)tables[i];
-    __syncthreads();
     const A *src = reinterpret_cast<const A *>(in);
     A *dst = reinterpret_cast<A *>(out);
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    for (uint64_t i0 = o0; i0 < o1; i0 += 4 * step) {
         A v[4];
         uint64_t idx[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint64_t i = i0 + u * stride;
+            const uint64_t i = i0 + u * step;
             idx[u] = i;
-            if (i < n) {
+            if (i < o1) {
                 I x = (I)bvec;
                 for (uint32_t b = 0; b < nbytes; ++b) x ^= tab[b * 256 + ((i >> (8 * b)) & 255u)];
                 v[u] = __ldg(&src[x]);
@@ -317,18 +339,36 @@ __global__ void __launch_bounds__(kThreads) gather_affine_kernel(const char *__r
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (idx[u] < n) dst[idx[u]] = v[u];
+            if (idx[u] < o1) dst[idx[u]] = v[u];
     }
 }
 
-// Bit-sliced gather.  A warp owns 1024 consecutive output indices per
-// iteration; lane l holds indices base + 32 l + j (j = 0..31) as bit planes:
-// plane b is a 32-bit word whose bit j is bit b of index base + 32 l + j.
-// Steps run last to first on the planes (target plane ^= AND of control
-// planes, each complemented for polarity 0); a 32x32 bit transpose turns the
-// planes back into 32 source indices, which the warp then gathers with
-// coalesced stores.  Planes live in shared memory, indexed by bit.
-constexpr int kSlicedChunk = 256;  // steps staged in shared memory at a time
+template <int B, bool WIDE>
+__global__ void __launch_bounds__(kThreads) gather_affine_kernel(const char *__restrict__ in,
+                                                                 char *__restrict__ out, uint64_t n,
+                                                                 const uint64_t *__restrict__ tables,
+                                                                 uint32_t nbytes, uint64_t bvec)
+{
+    using I = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    __shared__ I tab[5 * 256];
+    for (uint32_t i = threadIdx.x; i < nbytes * 256; i += kThreads) tab[i] = (I)tables[i];
+    __syncthreads();
+    affine_range<B, WIDE, I>(in, out, (uint64_t)blockIdx.x * kThreads + threadIdx.x, n,
+                             (uint64_t)gridDim.x * kThreads, tab, nbytes, bvec);
+}
+
+// Bit-sliced gather.  Each thread owns 64 consecutive output indices
+// my + j (j = 0..63) as bit planes: plane b is a 64-bit word whose bit j is
+// bit b of index my + j.  Steps run last to first on the planes (target
+// plane ^= AND of the control planes, a control on |0> complemented); two
+// 32x32 bit transposes turn the planes back into 64 source indices, which
+// the warp exchanges through shared memory so that every store instruction
+// writes 32 consecutive amplitudes.  Planes live in shared memory as
+// [plane][thread] words; plane M is all ones and stands in for absent
+// controls, so the common steps (<= 2 controls, all on |1>) run without
+// branches.
+constexpr int kSlicedChunk = 256;            // steps staged in shared memory at a time
+constexpr uint64_t kSlicedOutputs = kThreads * 64;  // outputs per CTA iteration
 
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32])
 {
@@ -347,18 +387,39 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32])
     }
 }
 
+__device__ __forceinline__ uint64_t lds64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void sts64(uint32_t addr, uint64_t v)
+{
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+constexpr uint32_t kPlaneStride = kThreads * 8;  // bytes between planes of one thread
+
+__host__ __device__ constexpr size_t sliced_smem_for(uint32_t M)
+{
+    return sizeof(uint64_t) * (size_t)(M + 1) * kThreads + sizeof(uint32_t) * 8 * 32 * 33 +
+           sizeof(SlicedStep) * kSlicedChunk + 8 * 32 * 33;
+}
+
+// One CTA: outputs [cbase, cbase + kSlicedOutputs) of a bit-sliced pass.
+// Every thread of the CTA must call it (it synchronises the CTA).
 template <int B, bool WIDE>
-__global__ void __launch_bounds__(kThreads) gather_sliced_kernel(
-    const char *__restrict__ in, char *__restrict__ out, uint32_t M, uint64_t n,
-    const SlicedStep *__restrict__ steps, uint32_t nsteps)
+__device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out, uint32_t M,
+                             uint64_t n, const SlicedStep *__restrict__ steps, uint32_t nsteps,
+                             uint64_t cbase, unsigned char *smem)
 {
     using A = typename AmpOf<B>::T;
-    extern __shared__ __align__(128) unsigned char smem[];
-    // planes: [M][kThreads] u32 ; table: [8 warps][32][33] u32 ; hi: [8][32][33] u8 ;
-    // step chunk: kSlicedChunk SlicedStep
+    // planes: [M + 1][kThreads] u64 ; table: [8 warps][32][33] u32 ;
+    // step chunk: kSlicedChunk SlicedStep ; hi: [8][32][33] u8 (WIDE)
     static_assert(kSlicedThreads == kThreads, "plane offsets assume kThreads threads");
-    uint32_t *planes = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *tabs = planes + (size_t)M * kThreads;
+    uint64_t *planes = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *tabs = reinterpret_cast<uint32_t *>(planes + (size_t)(M + 1) * kThreads);
     SlicedStep *chunk = reinterpret_cast<SlicedStep *>(tabs + 8 * 32 * 33);
     uint8_t *his = reinterpret_cast<uint8_t *>(chunk + kSlicedChunk);
 
@@ -367,63 +428,76 @@ __global__ void __launch_bounds__(kThreads) gather_sliced_kernel(
     uint8_t *hi = his + warp * 32 * 33;
     const A *src = reinterpret_cast<const A *>(in);
     A *dst = reinterpret_cast<A *>(out);
-    unsigned char *pl = reinterpret_cast<unsigned char *>(planes) + tid * 4;
-    const uint64_t per_iter = (uint64_t)gridDim.x * kThreads * 32;
+    const uint32_t pbase = smem_addr(planes) + tid * 8;  // this thread's plane 0
 
-    for (uint64_t cbase = (uint64_t)blockIdx.x * kThreads * 32; cbase < n; cbase += per_iter) {
-        // every thread of the CTA iterates the same number of times (uniform
-        // loop bound) so the step-chunk barriers below are safe.
-        const uint64_t my = cbase + (uint64_t)tid * 32;  // first index of this lane
-        // initial planes: bits 0..4 enumerate j, higher bits copy 'my'
-        const uint32_t pat[5] = {0xaaaaaaaau, 0xccccccccu, 0xf0f0f0f0u, 0xff00ff00u, 0xffff0000u};
-        for (uint32_t b = 0; b < M; ++b) {
-            const uint32_t w = (b < 5) ? pat[b] : (((my >> b) & 1ull) ? 0xffffffffu : 0u);
-            planes[b * kThreads + tid] = w;
-        }
-        // steps, last to first, staged in chunks
-        for (int64_t s_end = (int64_t)nsteps; s_end > 0; s_end -= kSlicedChunk) {
-            const int64_t s_beg = s_end > kSlicedChunk ? s_end - kSlicedChunk : 0;
-            const int cn = (int)(s_end - s_beg);
-            __syncthreads();
-            for (int i = tid; i < cn; i += kThreads) chunk[i] = steps[s_beg + i];
-            __syncthreads();
-            for (int q = cn - 1; q >= 0; --q) {
-                const SlicedStep d = chunk[q];
-                uint32_t m = 0xffffffffu;
+    const uint64_t my = cbase + (uint64_t)tid * 64;
+    // bits 0..5 enumerate j; higher bits are those of 'my'
+    const uint64_t pat[6] = {0xaaaaaaaaaaaaaaaaull, 0xccccccccccccccccull,
+                             0xf0f0f0f0f0f0f0f0ull, 0xff00ff00ff00ff00ull,
+                             0xffff0000ffff0000ull, 0xffffffff00000000ull};
+    __syncthreads();  // the previous user of this shared memory is done
 #pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    if (c >= d.nc) break;
-                    const uint32_t v = *reinterpret_cast<const uint32_t *>(pl + d.c_off[c]);
-                    m &= ((d.neg >> c) & 1) ? ~v : v;
+    for (uint32_t b = 0; b < 6; ++b)
+        if (b < M) sts64(pbase + b * kPlaneStride, pat[b]);
+    for (uint32_t b = 6; b < M; ++b)
+        sts64(pbase + b * kPlaneStride, ((my >> b) & 1ull) ? ~0ull : 0ull);
+    sts64(pbase + M * kPlaneStride, ~0ull);  // the all-ones plane
+    for (int64_t s_end = (int64_t)nsteps; s_end > 0; s_end -= kSlicedChunk) {
+        const int64_t s_beg = s_end > kSlicedChunk ? s_end - kSlicedChunk : 0;
+        const int cn = (int)(s_end - s_beg);
+        __syncthreads();
+        for (int i = tid; i < cn; i += kThreads) chunk[i] = steps[s_beg + i];
+        __syncthreads();
+#pragma unroll 2
+        for (int q = cn - 1; q >= 0; --q) {
+            const uint4 d = *reinterpret_cast<const uint4 *>(&chunk[q]);
+            // d.x: target | nc << 8 | neg << 16 | slow << 24 ; d.y, d.z: control planes
+            const uint32_t ta = pbase + (d.x & 0xffu) * kPlaneStride;
+            uint64_t m;
+            if (!(d.x >> 24)) {
+                m = lds64(pbase + (d.y & 0xffu) * kPlaneStride) &
+                    lds64(pbase + ((d.y >> 8) & 0xffu) * kPlaneStride);
+            } else {
+                const uint32_t nc = (d.x >> 8) & 0xffu, neg = (d.x >> 16) & 0xffu;
+                m = ~0ull;
+                for (uint32_t c = 0; c < nc; ++c) {
+                    const uint32_t cp = ((c < 4 ? d.y : d.z) >> (8 * (c & 3))) & 0xffu;
+                    const uint64_t v = lds64(pbase + cp * kPlaneStride);
+                    m &= ((neg >> c) & 1u) ? ~v : v;
                 }
-                *reinterpret_cast<uint32_t *>(pl + d.t_off) ^= m;
             }
+            sts64(ta, lds64(ta) ^ m);
         }
-        // planes -> 32 source indices of this lane
+    }
+    // planes -> 64 source indices, 32 at a time, exchanged for coalesced stores
+    const uint64_t wbase = cbase + (uint64_t)warp * 32 * 64;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
         uint32_t r[32];
 #pragma unroll
-        for (int b = 0; b < 32; ++b) r[b] = (b < (int)M) ? planes[b * kThreads + tid] : 0u;
+        for (int b = 0; b < 32; ++b)
+            r[b] = (b < (int)M) ? (uint32_t)(lds64(pbase + b * kPlaneStride) >> (32 * half)) : 0u;
         transpose32(r);
+        __syncwarp();
 #pragma unroll
         for (int j = 0; j < 32; ++j) tab[lane * 33 + j] = r[j];
         if (WIDE) {
-            const uint32_t w32 = (M > 32) ? planes[32 * kThreads + tid] : 0u;
-            const uint32_t w33 = (M > 33) ? planes[33 * kThreads + tid] : 0u;
+            const uint32_t w32 = (M > 32) ? (uint32_t)(lds64(pbase + 32 * kPlaneStride) >> (32 * half)) : 0u;
+            const uint32_t w33 = (M > 33) ? (uint32_t)(lds64(pbase + 33 * kPlaneStride) >> (32 * half)) : 0u;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
                 hi[lane * 33 + j] = (uint8_t)(((w32 >> j) & 1u) | (((w33 >> j) & 1u) << 1));
         }
         __syncwarp();
-        // coalesced gather: entry e of every lane's row -> outputs
-        const uint64_t wbase = cbase + (uint64_t)warp * 1024;
-#pragma unroll 4
+        // row e of the table holds lane e's indices my_e + 32 half + (0..31)
+#pragma unroll 1
         for (int e0 = 0; e0 < 32; e0 += 8) {
             A v[8];
             uint64_t o[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u;
-                o[u] = wbase + (uint64_t)e * 32 + lane;
+                o[u] = wbase + (uint64_t)e * 64 + 32 * half + lane;
                 uint64_t x = tab[e * 33 + lane];
                 if (WIDE) x |= (uint64_t)hi[e * 33 + lane] << 32;
                 if (o[u] < n) v[u] = __ldg(&src[x]);
@@ -432,7 +506,82 @@ __global__ void __launch_bounds__(kThreads) gather_sliced_kernel(
             for (int u = 0; u < 8; ++u)
                 if (o[u] < n) dst[o[u]] = v[u];
         }
-        __syncwarp();
+    }
+    __syncwarp();
+}
+
+template <int B, bool WIDE>
+__global__ void __launch_bounds__(kThreads, 2) gather_sliced_kernel(
+    const char *__restrict__ in, char *__restrict__ out, uint32_t M, uint64_t n,
+    const SlicedStep *__restrict__ steps, uint32_t nsteps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint64_t per_iter = (uint64_t)gridDim.x * kSlicedOutputs;
+    // the loop bound is uniform over the CTA, so the barriers inside are safe
+    for (uint64_t cbase = (uint64_t)blockIdx.x * kSlicedOutputs; cbase < n; cbase += per_iter)
+        sliced_chunk<B, WIDE>(in, out, M, n, steps, nsteps, cbase, smem);
+}
+
+// Sweep of pair indices [q0, q1) of one step (in place).
+template <int B>
+__device__ __forceinline__ void sweep_range(char *__restrict__ state, const SweepParams &p,
+                                            uint64_t q0, uint64_t q1, uint64_t step)
+{
+    using A = typename AmpOf<B>::T;
+    A *st = reinterpret_cast<A *>(state);
+    for (uint64_t q = q0; q < q1; q += step) {
+        uint64_t j = q;
+        for (uint32_t s = 0; s < p.nins; ++s) j = insert_zero(j, p.ins[s]);
+        j |= p.pol;
+        const A a = st[j];
+        const A b = st[j + p.half];
+        st[j] = b;
+        st[j + p.half] = a;
+    }
+}
+
+// ============================================================================
+// batched execution: one persistent launch over the passes of many circuits
+// ============================================================================
+
+// CTAs take work items (a range of outputs of one circuit's pass) from a
+// global counter until the level's list is exhausted; the affine tables of
+// the last circuit served stay in shared memory.
+template <int B, bool WIDE>
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__restrict__ passes,
+                                                         const BatchItem *__restrict__ items,
+                                                         uint32_t n_items, uint32_t *counter)
+{
+    using I = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_item;
+    __shared__ int32_t s_tables;  // pass whose affine tables are loaded, -1 none
+    I *tab = reinterpret_cast<I *>(smem);
+    if (threadIdx.x == 0) s_tables = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= n_items) break;
+        const BatchItem item = items[it];
+        const BatchPass &P = passes[item.pass];
+        const uint64_t o1 = item.start + item.count;
+        if (P.kind == 3) {
+            if (s_tables != (int32_t)item.pass) {
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < P.nbytes * 256; i += kThreads) tab[i] = (I)P.tables[i];
+                __syncthreads();
+                if (threadIdx.x == 0) s_tables = (int32_t)item.pass;
+            }
+            affine_range<B, WIDE, I>(P.in, P.out, item.start + threadIdx.x, o1, kThreads, tab,
+                                     P.nbytes, P.bvec);
+        } else if (P.kind == 4) {
+            if (threadIdx.x == 0) s_tables = -1;
+            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem);
+        } else {
+            sweep_range<B>(P.out, P.sweep, item.start + threadIdx.x, o1, kThreads);
+        }
     }
 }
 
@@ -443,6 +592,22 @@ __global__ void __launch_bounds__(kThreads) gather_sliced_kernel(
 constexpr int kProbBlocks = 1024;
 
 template <int B>
+__device__ __forceinline__ double prob_of(const char *__restrict__ state, uint64_t i)
+{
+    double re, im;
+    if (B == 8) {
+        const float2 v = __ldcs(reinterpret_cast<const float2 *>(state) + i);
+        re = (double)v.x;
+        im = (double)v.y;
+    } else {
+        const double2 v = __ldcs(reinterpret_cast<const double2 *>(state) + i);
+        re = v.x;
+        im = v.y;
+    }
+    return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+}
+
+template <int B>
 __global__ void __launch_bounds__(kThreads) probs_kernel(const char *__restrict__ state,
                                                          double *__restrict__ probs, uint64_t n,
                                                          double *__restrict__ partials)
@@ -450,19 +615,20 @@ __global__ void __launch_bounds__(kThreads) probs_kernel(const char *__restrict_
     __shared__ double red[kThreads];
     double acc = 0.0;
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
-        double re, im;
-        if (B == 8) {
-            const float2 v = reinterpret_cast<const float2 *>(state)[i];
-            re = (double)v.x;
-            im = (double)v.y;
-        } else {
-            const double2 v = reinterpret_cast<const double2 *>(state)[i];
-            re = v.x;
-            im = v.y;
+    uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {  // four independent loads in flight
+        double p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = prob_of<B>(state, i + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (probs) __stcs(probs + i + u * stride, p[u]);
+            acc += p[u];
         }
-        const double p = __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
-        if (probs) probs[i] = p;
+    }
+    for (; i < n; i += stride) {
+        const double p = prob_of<B>(state, i);
+        if (probs) __stcs(probs + i, p);
         acc += p;
     }
     red[threadIdx.x] = acc;
@@ -532,7 +698,7 @@ size_t tile_smem_bytes(int amp_bytes, int k)
     const uint32_t st = tile_stages(amp_bytes, k);
     return ((size_t)amp_bytes << k) * st + sizeof(uint64_t) * (1u << kMaxHighBits) +
            sizeof(TileStageMeta) * st + sizeof(uint64_t) * st + sizeof(TileStep) * kMaxTileSteps +
-           sizeof(uint2) * kMaxTileSteps * (st + 1);
+           sizeof(uint32_t) * kMaxOutBits + sizeof(uint16_t) * ((size_t)1 << k);
 }
 
 int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d_steps,
@@ -549,7 +715,9 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     p.nsteps = t.nsteps;
     p.all_local = t.all_local;
     p.stages = tile_stages(amp_bytes, (int)t.k);
+    p.nout = t.nout;
     for (int i = 0; i < kMaxHighBits; ++i) p.high[i] = t.high[i];
+    for (int i = 0; i < kMaxOutBits; ++i) p.outpos[i] = i < (int)t.nout ? t.outpos[i] : 0u;
     const size_t smem = tile_smem_bytes(amp_bytes, (int)t.k);
     const uint64_t cap = (uint64_t)num_sms();
     const int grid = (int)(t.n_tiles < cap ? t.n_tiles : cap);
@@ -559,21 +727,17 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
         e = cudaFuncSetAttribute(tile_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<8><<<grid, kThreads, smem, s>>>(p);
+        tile_kernel<8><<<grid, kTileThreads, smem, s>>>(p);
     } else {
         e = cudaFuncSetAttribute(tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<16><<<grid, kThreads, smem, s>>>(p);
+        tile_kernel<16><<<grid, kTileThreads, smem, s>>>(p);
     }
     return cudaGetLastError();
 }
 
-static size_t sliced_smem_bytes(uint32_t M)
-{
-    return sizeof(uint32_t) * ((size_t)M * kThreads + 8 * 32 * 33) +
-           sizeof(SlicedStep) * kSlicedChunk + 8 * 32 * 33;
-}
+static size_t sliced_smem_bytes(uint32_t M) { return sliced_smem_for(M); }
 
 template <int B, bool W>
 static cudaError_t launch_sliced(const void *in, void *out, uint32_t M, uint64_t n,
@@ -587,7 +751,7 @@ static cudaError_t launch_sliced(const void *in, void *out, uint32_t M, uint64_t
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_sliced_kernel<B, W>, kThreads,
                                                   smem);
     if (per_sm < 1) per_sm = 1;
-    const uint64_t chunks = (n + kThreads * 32 - 1) / (kThreads * 32);
+    const uint64_t chunks = (n + kSlicedOutputs - 1) / kSlicedOutputs;
     const uint64_t cap = (uint64_t)num_sms() * per_sm;
     const int grid = (int)(chunks < cap ? chunks : cap);
     gather_sliced_kernel<B, W><<<grid, kThreads, smem, s>>>(
@@ -648,6 +812,41 @@ int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d
     if (e != cudaSuccess) return e;
     reduce_kernel<<<1, kThreads, 0, s>>>(d_partials, (int)grid, d_norm);
     return cudaGetLastError();
+}
+
+size_t batch_smem_bytes(uint32_t max_sliced_M)
+{
+    const size_t tabs = 5 * 256 * sizeof(uint64_t);
+    const size_t sl = max_sliced_M ? sliced_smem_for(max_sliced_M) : 0;
+    return tabs > sl ? tabs : sl;
+}
+
+template <int B, bool W>
+static cudaError_t launch_batch_t(const BatchPass *passes, const BatchItem *items, uint32_t n_items,
+                                  uint32_t *counter, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<B, W>, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t cap = (uint64_t)num_sms() * per_sm;
+    const int grid = (int)(n_items < cap ? n_items : cap);
+    if (grid < 1) return cudaSuccess;
+    batch_kernel<B, W><<<grid, kThreads, smem, s>>>(passes, items, n_items, counter);
+    return cudaGetLastError();
+}
+
+int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
+                       uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (amp_bytes == 8)
+        return wide ? launch_batch_t<8, true>(d_passes, d_items, n_items, d_counter, smem, s)
+                    : launch_batch_t<8, false>(d_passes, d_items, n_items, d_counter, smem, s);
+    return wide ? launch_batch_t<16, true>(d_passes, d_items, n_items, d_counter, smem, s)
+                : launch_batch_t<16, false>(d_passes, d_items, n_items, d_counter, smem, s);
 }
 
 }  // namespace qsim

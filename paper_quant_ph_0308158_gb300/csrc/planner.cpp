@@ -183,6 +183,17 @@ void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &
         plan->tile_steps.push_back(ts);
     }
     t.all_local = all_local ? 1u : 0u;
+    // tile-id bit order: out-of-tile bits that no step controls vary fastest,
+    // control bits slowest (runs of tiles with the same active steps)
+    uint64_t ctl_out = 0;
+    for (uint32_t j = 0; j < t.nsteps; ++j) ctl_out |= plan->tile_steps[t.step_off + j].co;
+    t.nout = 0;
+    for (int pass2 = 0; pass2 < 2; ++pass2)
+        for (uint32_t b = 0; b < M; ++b) {
+            if ((tile_mask >> b) & 1ull) continue;
+            const bool is_ctl = (ctl_out >> b) & 1ull;
+            if (is_ctl == (pass2 == 1)) t.outpos[t.nout++] = b;
+        }
     // fraction of tiles that have at least one active step
     double touched = 1.0;
     if (!all_local) {
@@ -191,11 +202,9 @@ void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &
         uint64_t seed = 0x5eed0000ull + plan->passes.size();
         for (int i = 0; i < samples; ++i) {
             const uint64_t tile = splitmix64(seed) & (t.n_tiles - 1);
-            uint64_t base = tile << g.l;
-            for (uint32_t q = 0; q < t.nh; ++q) {
-                const uint32_t pos = t.high[q];
-                base = ((base >> pos) << (pos + 1)) | (base & ((1ull << pos) - 1ull));
-            }
+            uint64_t base = 0;
+            for (uint32_t q = 0; q < t.nout; ++q)
+                if ((tile >> q) & 1ull) base |= 1ull << t.outpos[q];
             for (uint32_t j = 0; j < t.nsteps; ++j) {
                 const TileStep &ts = plan->tile_steps[t.step_off + j];
                 if ((base & ts.co) == ts.po) {
@@ -326,17 +335,37 @@ void emit_sliced(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
     for (size_t q = 0; q < seg.size(); ++q) {
         const qsim_step &s = steps[seg[q]];
         SlicedStep h{};
-        h.t_off = (uint16_t)(s.target * kSlicedThreads * 4);
-        int c = 0;
+        uint32_t cp[kSlicedMaxControls];
+        for (int c = 0; c < kSlicedMaxControls; ++c) cp[c] = M;  // the all-ones plane
+        uint32_t nc = 0, neg = 0;
         for (uint64_t m = s.ctrl_mask; m; m &= m - 1) {
             const uint32_t b = (uint32_t)__builtin_ctzll(m);
-            h.c_off[c] = (uint16_t)(b * kSlicedThreads * 4);
-            if (!((s.ctrl_pol >> b) & 1ull)) h.neg |= (uint8_t)(1u << c);
-            ++c;
+            if (!((s.ctrl_pol >> b) & 1ull)) neg |= 1u << nc;
+            cp[nc++] = b;
         }
-        h.nc = (uint8_t)c;
+        const uint32_t slow = (nc > 2 || neg) ? 1u : 0u;
+        h.x = s.target | (nc << 8) | (neg << 16) | (slow << 24);
+        h.y = cp[0] | (cp[1] << 8) | (cp[2] << 16) | (cp[3] << 24);
+        h.z = cp[4] | (cp[5] << 8) | (cp[6] << 16) | (cp[7] << 24);
         plan->sliced_steps.push_back(h);
     }
+    p.nsteps = (uint32_t)seg.size();
+    p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+    plan->passes.push_back(p);
+}
+
+// A gather segment compiled into its own kernel (jit.cu): the plan keeps the
+// steps in circuit order; the kernel applies them last to first.
+void emit_compiled(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &seg,
+                   const PlanOptions &o, Plan *plan)
+{
+    Pass p{};
+    p.kind = kGather;
+    GatherPass &gp = p.gather;
+    gp.jit = 1;
+    gp.jit_off = (uint32_t)plan->jit_steps.size();
+    gp.jit_n = (uint32_t)seg.size();
+    for (uint64_t idx : seg) plan->jit_steps.push_back(steps[idx]);
     p.nsteps = (uint32_t)seg.size();
     p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
     plan->passes.push_back(p);
@@ -368,6 +397,8 @@ void plan_gather(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
         std::vector<uint64_t> seg(order.begin() + i, order.begin() + j);
         if (affine)
             emit_affine(M, steps, seg, o, plan);
+        else if (o.jit && M >= 10 && (int)seg.size() >= o.jit_min_steps)
+            emit_compiled(M, steps, seg, o, plan);
         else
             emit_sliced(M, steps, seg, o, plan);
         for (uint64_t idx : seg) plan->order.push_back(idx);
@@ -443,6 +474,13 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
     }
     *plan = std::move(tp);
     return QSIM_OK;
+}
+
+uint32_t pass_variant(const Pass &p)
+{
+    if (p.kind != kGather) return (uint32_t)p.kind;
+    if (p.gather.affine) return 3;
+    return p.gather.jit ? 5 : 4;
 }
 
 }  // namespace qsim

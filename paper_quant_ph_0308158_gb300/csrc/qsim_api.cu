@@ -291,6 +291,40 @@ int qsim_set_strategy(qsim_ctx *c, int strategy, int tile_bits, int low_bits)
     return plan_options(strategy, tile_bits, low_bits, &c->opts);
 }
 
+int qsim_set_jit(qsim_ctx *c, int enable)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    c->opts.jit = enable != 0;
+    return QSIM_OK;
+}
+
+int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L, int canonicalize,
+                        double *compile_ms)
+{
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    PlanOptions o;
+    o.amp_bytes = amp;
+    o.scratch_available = true;
+    o.strategy = QSIM_STRATEGY_GATHER;
+    o.jit = true;
+    o.cancel_adjacent = canonicalize != 0;
+    Plan plan;
+    std::string msg;
+    int rc = make_plan(M, steps, L, o, &plan, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    double total = 0;
+    for (const Pass &p : plan.passes) {
+        if (p.kind != kGather || !p.gather.jit) continue;
+        double ms = 0;
+        rc = jit_compile(M, (int)amp, plan.jit_steps.data() + p.gather.jit_off, p.gather.jit_n, &ms, &msg);
+        if (rc != QSIM_OK) return fail(rc, msg);
+        total += ms;
+    }
+    if (compile_ms) *compile_ms = total;
+    return QSIM_OK;
+}
+
 int qsim_set_canonicalize(qsim_ctx *c, int enable)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
@@ -364,13 +398,20 @@ int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
         int e = cudaSuccess;
         if (c->profiling) {
             QSIM_CUDA(cudaEventRecord(c->ev[2 * (prof0 + pi)], c->stream), "cudaEventRecord");
-            c->prof_kinds.push_back((uint32_t)p.kind);
+            c->prof_kinds.push_back(pass_variant(p));
             c->prof_bytes.push_back(p.alg_bytes);
         }
         if (p.kind == kSweep) {
             e = launch_sweep(c->buf[c->cur], (int)c->amp, p.sweep, c->d_err, c->stream);
         } else if (p.kind == kTile) {
             e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, c->stream);
+        } else if (p.gather.jit) {
+            std::string jmsg;
+            const int jrc = launch_jit_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M,
+                                              plan.jit_steps.data() + p.gather.jit_off,
+                                              p.gather.jit_n, c->stream, &jmsg);
+            if (jrc != QSIM_OK) return fail(jrc, jmsg);
+            c->cur = 1 - c->cur;
         } else {
             e = launch_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M, p.gather,
                               d_tab, d_sliced, c->d_err, c->stream);

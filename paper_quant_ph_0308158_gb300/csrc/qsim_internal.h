@@ -42,16 +42,19 @@ struct TileStep {
 };
 static_assert(sizeof(TileStep) == 32, "TileStep layout");
 
-// A step of a bit-sliced gather pass (16 bytes).  Bit planes are stored as
-// [bit][thread] 32-bit words in shared memory; offsets are byte offsets of a
-// plane for thread 0.
+// A step of a bit-sliced gather pass (16 bytes).  Bit planes live in shared
+// memory as [plane][thread] words; plane M is all ones and stands in for an
+// absent control.  Word x: target plane | nc << 8 | neg << 16 | slow << 24,
+// where neg bit q marks control q as firing on |0> and slow is set when the
+// step has more than two controls or any control on |0>.  Words y and z hold
+// control planes 0..3 and 4..7 (one byte each; unused bytes = plane M).
 constexpr int kSlicedThreads = 256;
-constexpr int kSlicedMaxControls = 6;
+constexpr int kSlicedMaxControls = 8;
 struct SlicedStep {
-    uint16_t t_off;    // target plane
-    uint8_t nc;        // number of controls (<= kSlicedMaxControls)
-    uint8_t neg;       // bit q set: control q fires on 0
-    uint16_t c_off[kSlicedMaxControls];
+    uint32_t x;
+    uint32_t y;
+    uint32_t z;
+    uint32_t pad;
 };
 static_assert(sizeof(SlicedStep) == 16, "SlicedStep layout");
 
@@ -66,6 +69,9 @@ struct SweepParams {
 struct TilePass {
     uint32_t k, l, nh;  // tile width, contiguous low bits, high bits
     uint32_t high[kMaxHighBits];
+    uint32_t nout;      // address bits outside the tile (M - k)
+    uint32_t outpos[40];  // their positions, in tile-id bit order: bits that
+                          // are controls of some step come last (slowest)
     uint64_t n_tiles;   // 2^(M-k)
     uint32_t step_off;  // offset of this pass's steps in the TileStep buffer
     uint32_t nsteps;
@@ -75,6 +81,9 @@ struct TilePass {
 
 struct GatherPass {
     uint32_t affine;     // 1: x(i) = A i ^ b through byte tables
+    uint32_t jit;        // 1: circuit-specialised compiled kernel (jit.cu)
+    uint32_t jit_off;    // offset of the segment's steps in Plan::jit_steps
+    uint32_t jit_n;      // number of those steps
     uint32_t nbytes;     // index bytes covered by tables (affine)
     uint32_t table_off;  // offset of 256 * nbytes entries in the table buffer
     uint32_t step_off;   // general: offset in the SlicedStep buffer
@@ -83,6 +92,9 @@ struct GatherPass {
 };
 
 enum PassKind : uint32_t { kSweep = 1, kTile = 2, kGather = 3 };
+// Kernel variant reported by tracing: 1 sweep, 2 tile, 3 affine gather,
+// 4 bit-sliced gather, 5 compiled gather.
+uint32_t pass_variant(const struct Pass &p);
 
 struct Pass {
     PassKind kind;
@@ -101,6 +113,8 @@ struct PlanOptions {
     size_t amp_bytes = 16;
     bool scratch_available = false;
     bool cancel_adjacent = true;
+    bool jit = false;        // compile non-affine gather segments (jit.cu)
+    int jit_min_steps = 32;  // shorter segments use the general kernel
 };
 
 struct Plan {
@@ -108,6 +122,7 @@ struct Plan {
     std::vector<TileStep> tile_steps;
     std::vector<SlicedStep> sliced_steps;
     std::vector<uint64_t> gather_tables;
+    std::vector<qsim_step> jit_steps;  // steps of compiled gather segments, circuit order
     std::vector<uint64_t> order;      // circuit step index of each applied step
     std::vector<uint64_t> pass_ends;  // exclusive end in 'order' of each pass
     uint64_t steps_in = 0;
@@ -118,6 +133,29 @@ struct Plan {
 int validate_steps(uint32_t M, const qsim_step *steps, size_t L, std::string *msg);
 int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &opt,
               Plan *plan, std::string *msg);
+
+// One circuit's pass inside a batched launch (batch.cu builds them).
+struct BatchPass {
+    const char *in;        // gather source (unused by sweeps)
+    char *out;             // gather destination / sweep state
+    uint32_t M;
+    uint32_t kind;         // 1 sweep, 3 affine gather, 4 bit-sliced gather
+    uint32_t nbytes;       // affine: table bytes
+    uint32_t nsteps;       // bit-sliced: steps
+    uint64_t bvec;         // affine: constant term
+    const uint64_t *tables;       // affine tables (device)
+    const SlicedStep *steps;      // bit-sliced steps (device)
+    SweepParams sweep;
+};
+// A work item: outputs (or sweep pairs) [start, start + count) of one pass;
+// bit-sliced items start on a multiple of 16384 outputs.
+struct BatchItem {
+    uint32_t pass;
+    uint32_t pad;
+    uint64_t start;
+    uint64_t count;
+};
+constexpr uint64_t kBatchItemOutputs = 16384;  // = 256 threads x 64 outputs
 
 // Message returned by qsim_last_error() on this host thread (qsim_api.cu).
 void set_last_error(const std::string &msg);
@@ -131,7 +169,16 @@ int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const Ga
 int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d_probs,
                          double *d_partials, int n_partials, double *d_norm, void *stream);
 int probabilities_partials_needed();
+size_t batch_smem_bytes(uint32_t max_sliced_M);
+int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
+                       uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream);
 size_t tile_smem_bytes(int amp_bytes, int k);
+
+// Compiled gather (jit.cu).  Return QSIM_OK or a QSIM_* error with msg set.
+int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *compile_ms,
+                std::string *msg);
+int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
+                      size_t n, void *stream, std::string *msg);
 int num_sms();
 
 }  // namespace qsim

@@ -276,10 +276,23 @@ def config_small_cnot(seed: int = 1):
                 steps=cnot_circuit(16, 64, seed), state_seed=seed)
 
 
+def config_cnot(M: int = 28, seed: int = 2, L: int = 1000, dtype=np.complex128):
+    """L controlled-NOTs (distinct uniform control/target) on a 2^M state."""
+    tag = "c128" if np.dtype(dtype) == np.complex128 else "c64"
+    return dict(name="M%d_%s_cnot%d" % (M, tag, L), M=M, dtype=dtype,
+                steps=cnot_circuit(M, L, seed), state_seed=seed)
+
+
+def config_mixed(M: int = 28, seed: int = 2, L: int = 1000, dtype=np.complex128):
+    """L steps of the NOT/CNOT/Toffoli/MCX mix on a 2^M state."""
+    tag = "c128" if np.dtype(dtype) == np.complex128 else "c64"
+    return dict(name="M%d_%s_mix%d" % (M, tag, L), M=M, dtype=dtype,
+                steps=mixed_circuit(M, L, seed), state_seed=seed)
+
+
 def config_mixed_m28(seed: int = 2, L: int = 1000):
     """M=28 complex128 (4 GiB), L=1000 steps of the NOT/CNOT/Toffoli/MCX mix."""
-    return dict(name="M28_c128_mix1000", M=28, dtype=np.complex128,
-                steps=mixed_circuit(28, L, seed), state_seed=seed)
+    return config_mixed(28, seed, L)
 
 
 def config_adder_m32(seed: int = 3):
@@ -287,6 +300,15 @@ def config_adder_m32(seed: int = 3):
     registers plus carry-in/out, two additions per unit, unit repeated 8x."""
     steps, l2b = adder_circuit(15, 2, 8, seed)
     return dict(name="M32_c64_adder15x16", M=32, dtype=np.complex64,
+                steps=steps, state_seed=seed, line_to_bit=l2b)
+
+
+def config_adder(n: int = 13, seed: int = 3):
+    """Ripple-carry adder on M = 2n + 2 bits, complex64, in place (the M = 32
+    workload scaled down: n = 13 gives M = 28, a 2 GiB state)."""
+    steps, l2b = adder_circuit(n, 2, 8, seed)
+    M = 2 * n + 2
+    return dict(name="M%d_c64_adder%dx16" % (M, n), M=M, dtype=np.complex64,
                 steps=steps, state_seed=seed, line_to_bit=l2b)
 
 

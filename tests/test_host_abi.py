@@ -96,7 +96,7 @@ def test_cnot_only_circuit_is_one_affine_gather_pass():
 
 def test_many_controls_fall_back_to_sweeps_inside_gather_plans():
     M = 12
-    many = W.make_steps([(0, 0b111111110, 0b101010110)])  # eight controls
+    many = W.make_steps([(0, 0b1111111110, 0b1010101110)])  # nine controls
     steps = np.concatenate([W.mixed_circuit(M, 10, 1), many, W.mixed_circuit(M, 10, 2)])
     plan = plan_circuit(M, np.complex128, steps, "gather")
     assert "sweep" in plan["kinds"] and "gather" in plan["kinds"]
@@ -143,3 +143,14 @@ def test_workload_plans_have_expected_shape():
     plan = plan_circuit(cfg["M"], cfg["dtype"], cfg["steps"], "inplace")
     assert plan["stats"]["steps_cancelled"] == 0
     assert plan["stats"]["tile_passes"] >= 1
+
+
+def test_jit_precompile_on_the_host():
+    from paper_quant_ph_0308158_gb300 import jit_precompile
+    steps = W.mixed_circuit(14, 100, 3)
+    ms = jit_precompile(14, np.complex128, steps)
+    assert ms >= 0.0
+    # a second call finds the compiled kernel cached
+    assert jit_precompile(14, np.complex128, steps) == ms
+    plan = plan_circuit(14, np.complex128, steps, "gather")
+    assert plan["kinds"] == ["gather"]
