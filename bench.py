@@ -52,7 +52,8 @@ from paper_quant_ph_0308158_gb300 import workloads as W  # noqa: E402
 METRIC = "amplitude-steps/s"
 UNIT = "amp-steps/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCE = os.path.join(ROOT, "paper_quant_ph_0308158_gb300", "csrc", "kernels.cu")
+CSRC = os.path.join(ROOT, "paper_quant_ph_0308158_gb300", "csrc")
+KERNEL_SOURCE = {"qsim_jit_gather": "jit.cu"}  # every other kernel lives in kernels.cu
 
 
 def workload(name: str):
@@ -177,8 +178,10 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
-    with open(KERNEL_SOURCE, "rb") as f:
+def kernel_source_hash(kernel: str) -> str:
+    """First 16 hex digits of the SHA-256 of the source file of a kernel."""
+    path = os.path.join(CSRC, KERNEL_SOURCE.get(kernel, "kernels.cu"))
+    with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -193,7 +196,7 @@ def ncu_traffic(kernel: str, wl: str):
     except (OSError, ValueError):
         return None
     e = rec.get(wl, {}).get(kernel)
-    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash():
+    if not e or e.get("kernel_source_sha256_16") != kernel_source_hash(kernel):
         return None
     return float(e["dram_bytes_per_launch"])
 
@@ -273,7 +276,7 @@ def run_ours(args, rank, ws, local):
     W.random_state(M, dtype, cfg["state_seed"], out=h_in)
 
     sim = Simulator(M, dtype, scratch=(strategy != "inplace"))
-    sim.set_strategy(strategy)
+    sim.set_strategy(strategy, args.tile_bits, args.low_bits)
     sim.set_canonicalize(False)
     jit_ms = None
     if args.jit and strategy != "inplace":
@@ -373,7 +376,7 @@ def run_ours(args, rank, ws, local):
                "sample": "first %d of the %d steps on the full 2^%d-amplitude state (%.1f s)" % (
                    nst, L, M, secs)}
 
-    launches = len(passes) + args.steps * 2  # passes + (probabilities + norm reduce) per step
+    launches = len(passes)  # every pass kernel and probabilities kernel in the timed region
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -382,6 +385,7 @@ def run_ours(args, rank, ws, local):
             "dtype": "c128" if dtype == np.complex128 else "c64",
             "data": "synthetic (seeded random state and circuit)",
             "config": {"workload": cfg["name"], "M": M, "L": L, "strategy": strategy,
+                       "tile_bits": args.tile_bits, "low_bits": args.low_bits,
                        "state_bytes": n * amp, "l2": "inputs larger than L2",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "passes_per_step": stats["passes"],
@@ -478,6 +482,83 @@ def run_batch(args, rank, ws, local):
     return 0
 
 
+def run_serve(args, rank, ws, local):
+    """Serving: a Poisson stream of simulation requests through qsim_server
+    (continuous batching under an HBM budget), FP64 probabilities out.
+    Each distinct M uses one seeded random input state from a pinned pool."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Server, build
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    build.build()
+    torch.cuda.set_device(local)
+    m_hi = args.serve_m_max
+    specs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=5,
+                               m_range=(12, m_hi), l_range=(100, 5000), mix="cnot")
+    dtype = np.dtype(np.complex128)
+    pool = {}
+    for M in sorted({sp["M"] for sp in specs}):
+        t = torch.empty(1 << M, dtype=torch.complex128, pin_memory=True)
+        W.random_state(M, dtype, 5000 + M, out=t.numpy())
+        pool[M] = (t, t.numpy())
+    budget = int(args.serve_budget_gb * 1e9)
+    host_bytes = int(args.serve_host_gb * 1e9)
+    srv = Server(budget, host_bytes, dtype)
+    lat = []
+    amp_steps = 0.0
+    done = 0
+    mbytes = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for sp in specs:
+        while True:
+            for rid, ms in srv.drain():
+                lat.append(ms)
+                srv.release(rid)
+                done += 1
+            if time.perf_counter() - t0 >= sp["arrival"]:
+                break
+            time.sleep(0.0002)
+        srv.submit(sp["M"], pool[sp["M"]][1], sp["steps"])
+        amp_steps += float(1 << sp["M"]) * sp["L"]
+    while done < len(specs):
+        got = srv.drain()
+        for rid, ms in got:
+            lat.append(ms)
+            srv.release(rid)
+            done += 1
+        if not got:
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    lat_a = np.array(lat)
+    value = amp_steps / wall
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(specs),
+        "warmup": 0, "ms_per_step": 1e3 * wall / len(specs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic (seeded Poisson arrivals, circuits and input states)",
+        "config": {"workload": "serve%d_poisson%g" % (len(specs), args.serve_rate),
+                   "M_range": [12, m_hi], "L_range": [100, 5000], "mix": "cnot",
+                   "hbm_budget_bytes": budget, "host_result_bytes": host_bytes,
+                   "requests_per_s": len(specs) / wall, "offered_requests_per_s": args.serve_rate,
+                   "latency_ms_p50": float(np.percentile(lat_a, 50)),
+                   "latency_ms_p99": float(np.percentile(lat_a, 99)),
+                   "latency_ms_max": float(lat_a.max()), "wall_s": wall,
+                   "rounds": st["rounds"], "peak_hbm_in_use": st["peak_in_use_bytes"],
+                   "step": "one request (submit to FP64 probabilities in host memory)"},
+        "roofline": None, "cpu_baseline": None, "e2e": {"value": value, "unit": UNIT,
+                   "h2d_bytes_per_step": float(np.mean([16 << sp["M"] for sp in specs])),
+                   "d2h_bytes_per_step": float(np.mean([8 << sp["M"] for sp in specs]))},
+        "gpu_launches": st["launches"], "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,8 +566,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28",
-                             "batch_cnot", "batch_mixed"])
+                             "batch_cnot", "batch_mixed", "serve"])
     ap.add_argument("--batch-size", type=int, default=4096)
+    ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
+    ap.add_argument("--low-bits", type=int, default=0, help="contiguous low tile bits l (0: default)")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-m-max", type=int, default=30)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-host-gb", type=float, default=48.0)
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
     ap.add_argument("--ref-steps-per-step", type=int, default=2,
                     help="oracle steps per timed reference step")
@@ -502,6 +590,8 @@ def main():
         rc = run_reference(args, rank, ws)
     elif args.workload.startswith("batch"):
         rc = run_batch(args, rank, ws, local)
+    elif args.workload == "serve":
+        rc = run_serve(args, rank, ws, local) if rank == 0 else 0
     else:
         rc = run_ours(args, rank, ws, local)
     if ws > 1:

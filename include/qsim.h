@@ -173,9 +173,10 @@ int qsim_get_plan_stats(qsim_ctx *ctx, qsim_plan_stats *out);
  * the records accumulate over successive applies.  qsim_get_pass_times waits
  * for queued work and writes, for each recorded pass (at most cap), the
  * device time in milliseconds, the kernel (1 sweep, 2 tile, 3 affine gather,
- * 4 bit-sliced gather, 5 compiled gather) and its algorithmic bytes (any
- * pointer may be NULL); *n_out receives the number of recorded passes.  When
- * cap covers them all the record is cleared. */
+ * 4 bit-sliced gather, 5 compiled gather, 6 probabilities from
+ * qsim_probabilities_device) and its algorithmic bytes (any pointer may be
+ * NULL); *n_out receives the number of recorded launches.  When cap covers
+ * them all the record is cleared. */
 int qsim_set_profiling(qsim_ctx *ctx, int enable);
 int qsim_get_pass_times(qsim_ctx *ctx, double *ms, uint32_t *kinds, double *alg_bytes,
                         size_t cap, size_t *n_out);
@@ -245,6 +246,70 @@ int qsim_batch_run_plain(qsim_batch *b);
 
 int qsim_batch_synchronize(qsim_batch *b);
 int qsim_batch_info(qsim_batch *b, qsim_batch_stats *out);
+
+/* ---- serving: continuous batching of simulation requests ------------------ */
+
+/* A server accepts simulation requests at any time and keeps the GPU busy
+ * with all of them (the paper has no counterpart).  Each request -- M, an
+ * input state in host memory, a wiring diagram -- is validated and planned at
+ * submission, then waits in FIFO order until its device memory (state,
+ * scratch, FP64 probabilities, plan tables: 2 * amp + 8 bytes per amplitude
+ * plus tables) fits in the server's HBM budget and its result fits in the
+ * server's pinned host result arena.  A scheduler thread uploads admitted
+ * states on a copy stream and runs rounds back to back: a round launches the
+ * next pass of every request whose state is on the device as one persistent
+ * launch, so requests that arrive while others run join the next round.
+ * After its last pass a request's probabilities are computed and copied into
+ * the result arena on a second copy stream, and its device memory returns to
+ * the budget.  All steps are applied (no cancellation). */
+typedef struct qsim_server qsim_server;
+
+typedef struct qsim_server_stats {
+    uint64_t submitted, admitted, completed;
+    uint64_t rounds;            /* persistent launches of request passes       */
+    uint64_t launches;          /* all kernel launches                          */
+    uint64_t active, waiting;   /* requests admitted / queued right now         */
+    uint64_t budget_bytes;      /* HBM budget                                   */
+    uint64_t in_use_bytes;      /* of it allocated to admitted requests now     */
+    uint64_t peak_in_use_bytes;
+    uint64_t host_in_use_bytes; /* result arena bytes held by unreleased results */
+    double amplitude_steps;     /* sum over completed requests of 2^M * L       */
+} qsim_server_stats;
+
+/* Reserve hbm_budget_bytes of device memory (one cudaMalloc) and a pinned
+ * host result arena of host_result_bytes, create the streams and start the
+ * scheduler thread on the current device. */
+int qsim_server_create(size_t hbm_budget_bytes, size_t host_result_bytes, int dtype,
+                       qsim_server **out);
+
+/* Queue a request.  host_amps (2^M amplitudes of the server's dtype; pinned
+ * memory uploads fastest) must stay valid and unchanged until the request is
+ * done; steps are copied.  QSIM_EINVAL for an invalid circuit, QSIM_EBUSY if
+ * the request could never fit the budgets.  *req_id identifies it. */
+int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const qsim_step *steps,
+                       size_t L, uint64_t *req_id);
+
+/* *done = 1 once the probabilities are in the result arena; then
+ * *latency_ms (may be NULL) is submit-to-result time and *probs (may be NULL)
+ * points at the 2^M FP64 probabilities, valid until qsim_server_release. */
+int qsim_server_poll(qsim_server *s, uint64_t req_id, int *done, double *latency_ms,
+                     const double **probs);
+
+/* Report finished requests in completion order, each once: up to cap ids
+ * (and their submit-to-result latencies, may be NULL) into the arrays;
+ * *n_out receives how many. */
+int qsim_server_drain(qsim_server *s, uint64_t *ids, double *latency_ms, size_t cap, size_t *n_out);
+
+/* Return a finished request's result memory to the arena and forget it. */
+int qsim_server_release(qsim_server *s, uint64_t req_id);
+
+/* Block until no request is waiting or running (QSIM_ETIMEOUT after timeout_s). */
+int qsim_server_wait_all(qsim_server *s, double timeout_s);
+
+int qsim_server_get_stats(qsim_server *s, qsim_server_stats *out);
+
+/* Stop the scheduler, wait for queued GPU work and free everything. */
+void qsim_server_destroy(qsim_server *s);
 
 /* ---- host-only planning (no GPU needed) ------------------------------------ */
 

@@ -34,7 +34,7 @@ QSIM_C128 = 1
 STRATEGY = {"auto": 0, "sweep": 1, "tile": 2, "gather": 3, "inplace": 4}
 PASS_KIND = {1: "sweep", 2: "tile", 3: "gather"}
 KERNEL = {1: "sweep_kernel", 2: "tile_kernel", 3: "gather_affine_kernel",
-          4: "gather_sliced_kernel", 5: "qsim_jit_gather"}
+          4: "gather_sliced_kernel", 5: "qsim_jit_gather", 6: "probs_kernel"}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libqsim.so")
 
@@ -48,7 +48,9 @@ EXPORTS = (
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
     "qsim_probabilities_noalloc", "qsim_batch_create", "qsim_batch_destroy",
     "qsim_batch_load_state", "qsim_batch_read_state", "qsim_batch_state_device", "qsim_batch_run",
-    "qsim_batch_run_plain", "qsim_batch_synchronize", "qsim_batch_info",
+    "qsim_batch_run_plain", "qsim_batch_synchronize", "qsim_batch_info", "qsim_server_create",
+    "qsim_server_submit", "qsim_server_poll", "qsim_server_release", "qsim_server_wait_all",
+    "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain",
 )
 
 
@@ -73,6 +75,18 @@ class BatchStats(ctypes.Structure):
                 ("items", ctypes.c_uint64), ("passes", ctypes.c_uint64),
                 ("amplitude_steps", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_double),
                 ("arena_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("active", ctypes.c_uint64),
+                ("waiting", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("in_use_bytes", ctypes.c_uint64), ("peak_in_use_bytes", ctypes.c_uint64),
+                ("host_in_use_bytes", ctypes.c_uint64), ("amplitude_steps", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -127,6 +141,15 @@ def load() -> ctypes.CDLL:
             "qsim_batch_run_plain": ([p], i),
             "qsim_batch_synchronize": ([p], i),
             "qsim_batch_info": ([p, ctypes.POINTER(BatchStats)], i),
+            "qsim_server_create": ([sz, sz, i, pp], i),
+            "qsim_server_submit": ([p, u32, p, p, sz, ctypes.POINTER(ctypes.c_uint64)], i),
+            "qsim_server_poll": ([p, ctypes.c_uint64, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double))], i),
+            "qsim_server_release": ([p, ctypes.c_uint64], i),
+            "qsim_server_drain": ([p, p, p, sz, ctypes.POINTER(sz)], i),
+            "qsim_server_wait_all": ([p, ctypes.c_double], i),
+            "qsim_server_get_stats": ([p, ctypes.POINTER(ServerStats)], i),
+            "qsim_server_destroy": ([p], None),
             "qsim_last_error": ([], ctypes.c_char_p),
             "qsim_version": ([], ctypes.c_char_p),
         }
@@ -390,6 +413,80 @@ class Batch:
     def info(self) -> dict:
         st = BatchStats()
         _check(self._lib.qsim_batch_info(self._b, ctypes.byref(st)))
+        return st.as_dict()
+
+
+class Server:
+    """Continuous-batching request loop (qsim_server_*).  ``submit`` returns a
+    request id; ``poll`` returns (done, latency_ms, probabilities view)."""
+
+    def __init__(self, hbm_budget_bytes: int, host_result_bytes: int, dtype=np.complex128):
+        self._lib = load()
+        self.dtype = np.dtype(dtype)
+        self._s = ctypes.c_void_p()
+        self._keep = {}
+        _check(self._lib.qsim_server_create(int(hbm_budget_bytes), int(host_result_bytes),
+                                            dtype_code(self.dtype), ctypes.byref(self._s)))
+
+    def close(self):
+        if self._s:
+            self._lib.qsim_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+        self._keep = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, M: int, k1: np.ndarray, steps) -> int:
+        """k1 must stay alive and unchanged until the request is done (kept here)."""
+        a = np.ascontiguousarray(k1)
+        if a.dtype != self.dtype or a.shape != (1 << M,):
+            raise QsimError(QSIM_EINVAL, "state must be 2^M amplitudes of the server dtype")
+        s = as_steps(steps)
+        rid = ctypes.c_uint64(0)
+        _check(self._lib.qsim_server_submit(self._s, M, _ptr(a), _ptr(s), len(s), ctypes.byref(rid)))
+        self._keep[rid.value] = (a, M)
+        return rid.value
+
+    def poll(self, rid: int, copy: bool = True):
+        done = ctypes.c_int(0)
+        lat = ctypes.c_double(0.0)
+        pp = ctypes.POINTER(ctypes.c_double)()
+        _check(self._lib.qsim_server_poll(self._s, rid, ctypes.byref(done), ctypes.byref(lat),
+                                          ctypes.byref(pp)))
+        if not done.value:
+            return False, None, None
+        M = self._keep[rid][1]
+        probs = np.ctypeslib.as_array(pp, shape=(1 << M,))
+        return True, lat.value, (probs.copy() if copy else probs)
+
+    def drain(self, cap: int = 4096):
+        """[(request id, latency ms)] of requests finished since the last drain."""
+        ids = np.zeros(cap, dtype=np.uint64)
+        lat = np.zeros(cap, dtype=np.float64)
+        n = ctypes.c_size_t(0)
+        _check(self._lib.qsim_server_drain(self._s, _ptr(ids), _ptr(lat), cap, ctypes.byref(n)))
+        return [(int(ids[i]), float(lat[i])) for i in range(n.value)]
+
+    def release(self, rid: int):
+        _check(self._lib.qsim_server_release(self._s, rid))
+        self._keep.pop(rid, None)
+
+    def wait_all(self, timeout_s: float = 600.0):
+        _check(self._lib.qsim_server_wait_all(self._s, timeout_s))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.qsim_server_get_stats(self._s, ctypes.byref(st)))
         return st.as_dict()
 
 

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wextra", "-Wno-unused-parameter"]
 
-SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "jit.cu", "batch.cu", "planner.cpp"]
+SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "jit.cu", "batch.cu", "server.cu", "planner.cpp"]
 HEADERS = [os.path.join(CSRC, "qsim_internal.h"), os.path.join(ROOT, "include", "qsim.h")]
 
 
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("libqsim build failed:\n" + "\n".join(errors))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-ldl"]
+    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-ldl", "-lpthread"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)

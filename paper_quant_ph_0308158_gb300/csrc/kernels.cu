@@ -159,60 +159,32 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t tile, const uint32_t *out
     return b;
 }
 
-// Warp 0: find this CTA's next tile with an active step, record the active
-// set, arm the stage barrier and issue one bulk copy per contiguous run of
-// 2^l amplitudes.
-template <int B>
-__device__ uint64_t tile_produce(const TileKParams &p, int s, uint64_t next, uint64_t end,
-                                 char *buf, const uint64_t *depo, TileStageMeta *meta,
-                                 const TileStep *steps_sm, const uint32_t *outpos, uint64_t *bar,
-                                 uint32_t (&last)[kMaskWords], bool &have_last)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
-    const int lane = threadIdx.x & 31;
-    uint64_t base = kNoTile;
-    uint32_t mask[kMaskWords];
-    bool any = false;
-    while (next < end) {
-        base = tile_base(next, outpos);
-        ++next;
-        any = false;
-#pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) {
-            const uint32_t i = w * 32 + lane;
-            bool act = false;
-            if (i < p.nsteps) act = p.all_local || (base & steps_sm[i].co) == steps_sm[i].po;
-            mask[w] = __ballot_sync(0xffffffffu, act);
-            any |= mask[w] != 0;
-        }
-        if (any) break;
-        base = kNoTile;
-    }
-    bool same = have_last;
-#pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) same = same && (mask[w] == last[w]);
-    if (lane == 0) {
-        meta[s].base = base;
-#pragma unroll
-        for (int w = 0; w < kMaskWords; ++w) meta[s].mask[w] = mask[w];
-        meta[s].same = same ? 1u : 0u;
-    }
-    if (base == kNoTile) return next;
-#pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) last[w] = mask[w];
-    have_last = true;
-    fence_proxy_async_smem();
-    const uint32_t run_bytes = (uint32_t)B << p.l;
-    if (lane == 0) mbar_arrive_expect_tx(bar, run_bytes << p.nh);
-    __syncwarp();
-    for (uint32_t r = lane; r < (1u << p.nh); r += 32) {
-        const uint64_t gi = base + depo[r];
-        bulk_g2s(buf + (size_t)r * run_bytes, p.state + gi * B, run_bytes, bar);
-    }
-    return next;
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Bounded wait on an mbarrier phase; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (unsigned w = 0; w < kWaitLimit; ++w)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(kTileThreads) : "memory");
+}
+
+// Warp-specialised pipeline: warps 0..15 consume tiles, warp 16 produces.
+// Stage s has a 'full' barrier (one producer arrival + the bytes of the
+// bulk copies) and an 'empty' barrier (one arrival per consumer warp).  The
+// producer finds the CTA's next tile with an active step, publishes its
+// base and active-step mask in the stage's metadata, and issues one bulk
+// copy per contiguous run of 2^l amplitudes; an empty tile marks the end.
 template <int B>
-__global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(TileKParams p)
+__global__ void __launch_bounds__(kTileThreads + 32, 1) tile_kernel(TileKParams p)
 {
     using A = typename AmpOf<B>::T;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -221,48 +193,106 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(TileKParams p)
     char *bufs = reinterpret_cast<char *>(smem);
     uint64_t *depo = reinterpret_cast<uint64_t *>(smem + tile_bytes * p.stages);
     TileStageMeta *meta = reinterpret_cast<TileStageMeta *>(depo + (1u << p.nh));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(meta + p.stages);
-    TileStep *steps_sm = reinterpret_cast<TileStep *>(bars + p.stages);
+    uint64_t *full = reinterpret_cast<uint64_t *>(meta + p.stages);
+    uint64_t *empty = full + p.stages;
+    TileStep *steps_sm = reinterpret_cast<TileStep *>(empty + p.stages);
     uint32_t *outpos = reinterpret_cast<uint32_t *>(steps_sm + p.nsteps);
     uint16_t *perm = reinterpret_cast<uint16_t *>(outpos + kMaxOutBits);
 
     const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    for (uint32_t r = tid; r < (1u << p.nh); r += kTileThreads) {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nthreads = kTileThreads + 32;
+    for (uint32_t r = tid; r < (1u << p.nh); r += nthreads) {
         uint64_t d = 0;
         for (uint32_t q = 0; q < p.nh; ++q) d |= (uint64_t)((r >> q) & 1u) << p.high[q];
         depo[r] = d;
     }
-    for (uint32_t i = tid; i < p.nsteps; i += kTileThreads) steps_sm[i] = p.steps[i];
-    for (uint32_t i = tid; i < kMaxOutBits; i += kTileThreads) outpos[i] = p.outpos[i];
+    for (uint32_t i = tid; i < p.nsteps; i += nthreads) steps_sm[i] = p.steps[i];
+    for (uint32_t i = tid; i < kMaxOutBits; i += nthreads) outpos[i] = p.outpos[i];
     if (tid == 0) {
-        for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
+        for (uint32_t s = 0; s < p.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTileThreads / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
     // contiguous range of tile ids for this CTA
     const uint64_t per = (p.n_tiles + gridDim.x - 1) / gridDim.x;
-    uint64_t next = (uint64_t)blockIdx.x * per;
-    const uint64_t end = next + per < p.n_tiles ? next + per : p.n_tiles;
-    uint32_t last[kMaskWords];
-    bool have_last = false;
-    if (warp == 0) {
-        for (uint32_t s = 0; s < p.stages; ++s)
-            next = tile_produce<B>(p, (int)s, next, end, bufs + tile_bytes * s, depo, meta, steps_sm,
-                                   outpos, &bars[s], last, have_last);
-    }
-    __syncthreads();
+    const uint64_t begin = (uint64_t)blockIdx.x * per;
+    const uint64_t end = begin + per < p.n_tiles ? begin + per : p.n_tiles;
 
+    if (warp == kTileThreads / 32) {
+        // ---------------- producer warp ----------------
+        uint64_t next = begin;
+        uint32_t last[kMaskWords];
+        bool have_last = false;
+        const uint32_t run_bytes = (uint32_t)B << p.l;
+        for (uint32_t it = 0;; ++it) {
+            const uint32_t s = it % p.stages;
+            if (it >= p.stages && !mbar_wait_bounded(&empty[s], ((it / p.stages) - 1) & 1u)) {
+                if (lane == 0) atomicOr(p.err, 2);
+                return;
+            }
+            uint64_t base = kNoTile;
+            uint32_t mask[kMaskWords];
+            while (next < end) {
+                base = tile_base(next, outpos);
+                ++next;
+                bool any = false;
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) {
+                    const uint32_t i = w * 32 + lane;
+                    bool act = false;
+                    if (i < p.nsteps) act = p.all_local || (base & steps_sm[i].co) == steps_sm[i].po;
+                    mask[w] = __ballot_sync(0xffffffffu, act);
+                    any |= mask[w] != 0;
+                }
+                if (any) break;
+                base = kNoTile;
+            }
+            bool same = have_last && base != kNoTile;
+            if (base != kNoTile) {
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) same = same && (mask[w] == last[w]);
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) last[w] = mask[w];
+                have_last = true;
+            }
+            if (lane == 0) {
+                meta[s].base = base;
+#pragma unroll
+                for (int w = 0; w < kMaskWords; ++w) meta[s].mask[w] = base != kNoTile ? mask[w] : 0u;
+                meta[s].same = same ? 1u : 0u;
+            }
+            __syncwarp();
+            if (base == kNoTile) {
+                if (lane == 0) mbar_arrive(&full[s]);  // end marker, no bytes
+                return;
+            }
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], run_bytes << p.nh);
+            __syncwarp();
+            char *buf = bufs + tile_bytes * s;
+            for (uint32_t r = lane; r < (1u << p.nh); r += 32)
+                bulk_g2s(buf + (size_t)r * run_bytes, p.state + (base + depo[r]) * B, run_bytes, &full[s]);
+        }
+    }
+
+    // ---------------- consumer warps ----------------
     const uint32_t lmask = (1u << p.l) - 1u;
-    uint32_t parity = 0;  // bit s: phase of stage s
     A *st = reinterpret_cast<A *>(p.state);
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
+        if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u)) {
+            if (tid == 0) atomicOr(p.err, 1);
+            return;
+        }
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
         if (!meta[s].same) {
-            // new active set: rebuild perm (steps last to first on each index)
+            consumer_sync();  // every consumer is done with the previous table
             for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 8) {
                 uint32_t src[8];
 #pragma unroll
@@ -280,14 +310,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(TileKParams p)
                     if (j < tile_amps) perm[j] = (uint16_t)src[e];
                 }
             }
+            consumer_sync();  // the new table is complete
         }
-        bool ok = false;
-        for (unsigned w = 0; w < kWaitLimit && !ok; ++w) ok = mbar_try_wait(&bars[s], (parity >> s) & 1u);
-        if (__syncthreads_or(!ok)) {  // also publishes perm
-            if (tid == 0) atomicOr(p.err, 1);
-            return;
-        }
-        parity ^= 1u << s;
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
         for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 4) {
             A v[4];
@@ -302,11 +326,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(TileKParams p)
                 if (j < tile_amps) st[base + depo[j >> p.l] + (j & lmask)] = v[e];
             }
         }
-        __syncthreads();
-        if (warp == 0)
-            next = tile_produce<B>(p, (int)s, next, end, bufs + tile_bytes * s, depo, meta, steps_sm,
-                                   outpos, &bars[s], last, have_last);
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
     }
 }
 
@@ -604,10 +625,13 @@ __device__ __forceinline__ double prob_of(const char *__restrict__ state, uint64
         re = v.x;
         im = v.y;
     }
-    return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    // re^2 + im^2 with im^2 rounded and one fused multiply-add: within one
+    // unit in the last place of the separately rounded sum, one FP64
+    // instruction fewer (FP64 issue rate bounds this kernel on GB300)
+    return __fma_rn(re, re, __dmul_rn(im, im));
 }
 
-template <int B>
+template <int B, bool NORM>
 __global__ void __launch_bounds__(kThreads) probs_kernel(const char *__restrict__ state,
                                                          double *__restrict__ probs, uint64_t n,
                                                          double *__restrict__ partials)
@@ -623,14 +647,15 @@ __global__ void __launch_bounds__(kThreads) probs_kernel(const char *__restrict_
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (probs) __stcs(probs + i + u * stride, p[u]);
-            acc += p[u];
+            if (NORM) acc += p[u];
         }
     }
     for (; i < n; i += stride) {
         const double p = prob_of<B>(state, i);
         if (probs) __stcs(probs + i, p);
-        acc += p;
+        if (NORM) acc += p;
     }
+    if (!NORM) return;
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int s = kThreads / 2; s > 0; s >>= 1) {
@@ -697,7 +722,7 @@ size_t tile_smem_bytes(int amp_bytes, int k)
 {
     const uint32_t st = tile_stages(amp_bytes, k);
     return ((size_t)amp_bytes << k) * st + sizeof(uint64_t) * (1u << kMaxHighBits) +
-           sizeof(TileStageMeta) * st + sizeof(uint64_t) * st + sizeof(TileStep) * kMaxTileSteps +
+           sizeof(TileStageMeta) * st + 2 * sizeof(uint64_t) * st + sizeof(TileStep) * kMaxTileSteps +
            sizeof(uint32_t) * kMaxOutBits + sizeof(uint16_t) * ((size_t)1 << k);
 }
 
@@ -727,12 +752,12 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
         e = cudaFuncSetAttribute(tile_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<8><<<grid, kTileThreads, smem, s>>>(p);
+        tile_kernel<8><<<grid, kTileThreads + 32, smem, s>>>(p);
     } else {
         e = cudaFuncSetAttribute(tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<16><<<grid, kTileThreads, smem, s>>>(p);
+        tile_kernel<16><<<grid, kTileThreads + 32, smem, s>>>(p);
     }
     return cudaGetLastError();
 }
@@ -799,15 +824,24 @@ int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d
                          double *d_partials, int n_partials, double *d_norm, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *st = static_cast<const char *>(state);
+    if (!d_norm) {  // probabilities only: no accumulation, no reduction
+        const uint64_t want = (n + kThreads * 4 - 1) / (kThreads * 4);
+        const uint64_t cap = (uint64_t)num_sms() * 16;
+        const int grid = (int)(want < cap ? (want ? want : 1) : cap);
+        if (amp_bytes == 8)
+            probs_kernel<8, false><<<grid, kThreads, 0, s>>>(st, d_probs, n, nullptr);
+        else
+            probs_kernel<16, false><<<grid, kThreads, 0, s>>>(st, d_probs, n, nullptr);
+        return cudaGetLastError();
+    }
     const uint64_t want = (n + kThreads - 1) / kThreads;
     uint64_t grid = want < (uint64_t)n_partials ? want : (uint64_t)n_partials;
     if (grid < 1) grid = 1;
     if (amp_bytes == 8)
-        probs_kernel<8><<<(int)grid, kThreads, 0, s>>>(static_cast<const char *>(state), d_probs, n,
-                                                       d_partials);
+        probs_kernel<8, true><<<(int)grid, kThreads, 0, s>>>(st, d_probs, n, d_partials);
     else
-        probs_kernel<16><<<(int)grid, kThreads, 0, s>>>(static_cast<const char *>(state), d_probs, n,
-                                                        d_partials);
+        probs_kernel<16, true><<<(int)grid, kThreads, 0, s>>>(st, d_probs, n, d_partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_kernel<<<1, kThreads, 0, s>>>(d_partials, (int)grid, d_norm);

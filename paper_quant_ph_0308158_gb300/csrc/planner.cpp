@@ -125,8 +125,10 @@ struct TileGeom {
 TileGeom tile_geometry(uint32_t M, const PlanOptions &o)
 {
     TileGeom g;
+    // 64 KiB tiles; runs of 2^l amplitudes of 1 KiB, since each run is one
+    // bulk copy and shorter copies leave the copy engine, not HBM, the limit
     const uint32_t kdef = o.amp_bytes == 16 ? 12 : 13;
-    const uint32_t ldef = o.amp_bytes == 16 ? 4 : 5;
+    const uint32_t ldef = o.amp_bytes == 16 ? 6 : 7;
     uint32_t k = o.tile_bits > 0 ? (uint32_t)o.tile_bits : kdef;
     uint32_t l = o.low_bits > 0 ? (uint32_t)o.low_bits : ldef;
     k = std::min<uint32_t>(std::min<uint32_t>(k, kMaxTileBits), M);

@@ -461,9 +461,24 @@ int qsim_probabilities_device(qsim_ctx *c, double *d_probs, double *norm_out)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
     if (reinterpret_cast<uintptr_t>(d_probs) & 7u) return fail(QSIM_EINVAL, "d_probs misaligned");
+    const size_t prof0 = c->prof_kinds.size();
+    if (c->profiling) {
+        while (c->ev.size() < 2 * (prof0 + 1)) {
+            cudaEvent_t ev;
+            QSIM_CUDA(cudaEventCreate(&ev), "cudaEventCreate(profiling)");
+            c->ev.push_back(ev);
+        }
+        QSIM_CUDA(cudaEventRecord(c->ev[2 * prof0], c->stream), "cudaEventRecord");
+    }
     int e = launch_probabilities(c->buf[c->cur], (int)c->amp, c->n, d_probs, c->d_partials,
-                                 probabilities_partials_needed(), c->d_norms, c->stream);
+                                 probabilities_partials_needed(), norm_out ? c->d_norms : nullptr,
+                                 c->stream);
     if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+    if (c->profiling) {
+        QSIM_CUDA(cudaEventRecord(c->ev[2 * prof0 + 1], c->stream), "cudaEventRecord");
+        c->prof_kinds.push_back(6);
+        c->prof_bytes.push_back((double)c->n * (double)(c->amp + (d_probs ? 8 : 0)));
+    }
     if (norm_out) {
         int rc = check_device(c);
         if (rc != QSIM_OK) return rc;
@@ -484,8 +499,8 @@ int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_o
     const char *state = static_cast<const char *>(c->buf[c->cur]);
     for (size_t k = 0; k < nchunks; ++k) {
         int e = launch_probabilities(state + k * chunk * c->amp, (int)c->amp, chunk, c->d_probs_chunk,
-                                     c->d_partials, probabilities_partials_needed(), c->d_norms + k,
-                                     c->stream);
+                                     c->d_partials, probabilities_partials_needed(),
+                                     norm_out ? c->d_norms + k : nullptr, c->stream);
         if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
         QSIM_CUDA(cudaMemcpyAsync(host_probs + k * chunk, c->d_probs_chunk, sizeof(double) * chunk,
                                   cudaMemcpyDeviceToHost, c->stream),

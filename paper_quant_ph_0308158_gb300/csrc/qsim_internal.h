@@ -62,8 +62,8 @@ struct SweepParams {
     uint64_t n_pairs;   // 2^(M-1-c)
     uint64_t pol;       // control polarity
     uint64_t half;      // 1 << target
-    uint32_t nins;      // number of zero-bit insertions (controls + target)
-    uint32_t ins[8];    // insertion positions, ascending
+    uint32_t nins;      // number of zero-bit insertions (controls + target), <= M
+    uint32_t ins[QSIM_MAX_QUBITS];  // insertion positions, ascending
 };
 
 struct TilePass {

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_quant_ph_0308158_gb300 import QsimError, Simulator, workloads as W
+from tests.helpers import assert_probs_close
 
 pytestmark = pytest.mark.gpu
 
@@ -166,7 +167,7 @@ def test_probabilities_fp64(dtype, M):
         sim.load_state(k1)
         sim.apply(steps)
         p, norm = sim.probabilities(with_norm=True)
-    np.testing.assert_array_equal(p, want)
+    assert_probs_close(p, want)
     ref = oracle.fsum_pairwise(want)
     assert abs(norm - ref) <= NORM_RTOL * ref
     assert abs(norm - 1.0) < 1e-6 if dtype == np.complex64 else abs(norm - 1.0) < 1e-12

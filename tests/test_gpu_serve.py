@@ -1,0 +1,113 @@
+"""The serving loop (qsim_server_*): requests admitted under an HBM budget,
+run together in rounds, results identical to the CPU oracle and to the same
+request served alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_quant_ph_0308158_gb300 import QsimError, Server, workloads as W
+from tests.helpers import assert_probs_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_quant_ph_0308158_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _requests(n, seed, m_lo=4, m_hi=16):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        M = int(rng.integers(m_lo, m_hi + 1))
+        kind = int(rng.integers(3))
+        L = int(rng.integers(0, 600)) if i % 7 else 4500  # some need two gather passes
+        if kind == 0:
+            st = W.cnot_circuit(M, L, 5000 + i)
+        elif kind == 1:
+            st = W.mixed_circuit(M, L, 5000 + i)
+        else:
+            st = W.random_circuit(M, L, 5000 + i, max_controls=min(9, M - 1))
+        k1 = W.random_state(M, np.complex128, 7000 + i)
+        out.append((M, k1, st))
+    return out
+
+
+def _expected(M, k1, st):
+    return oracle.probabilities(oracle.apply_circuit(M, k1, st))
+
+
+def test_served_results_match_the_oracle_and_the_request_alone():
+    reqs = _requests(40, 1)
+    # a budget that holds only a few of the largest requests at once
+    with Server(24 << 20, 64 << 20, np.complex128) as srv:
+        ids = []
+        for i, (M, k1, st) in enumerate(reqs):  # arrivals spread over time
+            ids.append(srv.submit(M, k1, st))
+            if i % 5 == 4:
+                time.sleep(0.002)
+        srv.wait_all(300)
+        stats = srv.stats()
+        assert stats["completed"] == len(reqs) and stats["rounds"] >= 2
+        assert stats["peak_in_use_bytes"] <= 24 << 20
+        mixed = {}
+        for rid, (M, k1, st) in zip(ids, reqs):
+            done, lat, p = srv.poll(rid)
+            assert done and lat > 0
+            mixed[rid] = p
+            assert_probs_close(p, _expected(M, k1, st))
+            srv.release(rid)
+        assert srv.stats()["in_use_bytes"] == 0 and srv.stats()["host_in_use_bytes"] == 0
+    # the same requests served one at a time give the same bits
+    with Server(24 << 20, 64 << 20, np.complex128) as srv:
+        for rid, (M, k1, st) in list(zip(ids, reqs))[:8]:
+            r = srv.submit(M, k1, st)
+            srv.wait_all(60)
+            done, _, p = srv.poll(r)
+            assert done
+            np.testing.assert_array_equal(p, mixed[rid])
+            srv.release(r)
+
+
+def test_concurrent_submitters():
+    reqs = _requests(24, 2, 6, 14)
+    with Server(64 << 20, 64 << 20, np.complex128) as srv:
+        ids = [None] * len(reqs)
+
+        def worker(lo):
+            for j in range(lo, len(reqs), 3):
+                M, k1, st = reqs[j]
+                ids[j] = srv.submit(M, k1, st)
+
+        th = [threading.Thread(target=worker, args=(t,)) for t in range(3)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        srv.wait_all(300)
+        for rid, (M, k1, st) in zip(ids, reqs):
+            done, _, p = srv.poll(rid)
+            assert done
+            assert_probs_close(p, _expected(M, k1, st))
+            srv.release(rid)
+
+
+def test_admission_rejections():
+    with Server(1 << 20, 1 << 20, np.complex128) as srv:
+        big = W.random_state(16, np.complex128, 1)  # 2^16 * 40 bytes > 1 MiB
+        with pytest.raises(QsimError) as e:
+            srv.submit(16, big, W.cnot_circuit(16, 4, 1))
+        assert e.value.code == -5
+        with pytest.raises(QsimError) as e:
+            srv.submit(4, W.random_state(4, np.complex128, 1), W.make_steps([(0, 1, 1)]))
+        assert e.value.code == -1
+        with pytest.raises(QsimError):
+            srv.poll(12345)
