@@ -15,9 +15,13 @@
 //                         indices at once in bit-sliced form, steps applied
 //                         last to first (Sec. 2h product, Sec. 2b gather).
 //   probs_kernel          p(i) = re^2 + im^2 in FP64 and a norm partial sum.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "qsim_internal.h"
@@ -84,6 +88,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
         : "memory");
 }
 
+// One box of a 5-dimensional tensor map into shared memory.
+__device__ __forceinline__ void tensor_g2s(void *dst_smem, const CUtensorMap *map, int c0, int c1,
+                                           int c2, int c3, int c4, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -140,6 +156,9 @@ struct TileKParams {
     uint32_t k, l, nh, nsteps, all_local, stages, nout;
     uint32_t high[kMaxHighBits];
     uint32_t outpos[kMaxOutBits];  // global bit of tile-id bit q
+    uint32_t tma, nrest, epa, box_bytes;
+    uint32_t start[6];             // tensor view: first address bit of each dimension
+    uint32_t rest_pos[kMaxHighBits];
 };
 
 struct TileStageMeta {
@@ -184,7 +203,8 @@ __device__ __forceinline__ void consumer_sync()
 // base and active-step mask in the stage's metadata, and issues one bulk
 // copy per contiguous run of 2^l amplitudes; an empty tile marks the end.
 template <int B>
-__global__ void __launch_bounds__(kTileThreads + 32, 1) tile_kernel(TileKParams p)
+__global__ void __launch_bounds__(kTileThreads + 32, 1)
+    tile_kernel(TileKParams p, const __grid_constant__ CUtensorMap tmap)
 {
     using A = typename AmpOf<B>::T;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -275,8 +295,27 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1) tile_kernel(TileKParams 
             if (lane == 0) mbar_arrive_expect_tx(&full[s], run_bytes << p.nh);
             __syncwarp();
             char *buf = bufs + tile_bytes * s;
-            for (uint32_t r = lane; r < (1u << p.nh); r += 32)
-                bulk_g2s(buf + (size_t)r * run_bytes, p.state + (base + depo[r]) * B, run_bytes, &full[s]);
+            if (p.tma) {
+                // one tensor copy per value of the enumerated tile bits
+                for (uint32_t r = lane; r < (1u << p.nrest); r += 32) {
+                    uint64_t g = base;
+                    for (uint32_t q = 0; q < p.nrest; ++q)
+                        if ((r >> q) & 1u) g |= 1ull << p.rest_pos[q];
+                    int c[5];
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+                        const uint32_t w = p.start[d + 1] - p.start[d];
+                        const uint64_t v = w ? ((g >> p.start[d]) & ((1ull << w) - 1ull)) : 0ull;
+                        c[d] = (int)(d == 0 ? v * p.epa : v);
+                    }
+                    tensor_g2s(buf + (size_t)r * p.box_bytes, &tmap, c[0], c[1], c[2], c[3], c[4],
+                               &full[s]);
+                }
+            } else {
+                for (uint32_t r = lane; r < (1u << p.nh); r += 32)
+                    bulk_g2s(buf + (size_t)r * run_bytes, p.state + (base + depo[r]) * B, run_bytes,
+                             &full[s]);
+            }
         }
     }
 
@@ -682,6 +721,22 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 
 int g_num_sms = 0;
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
 }  // namespace
 
 int num_sms()
@@ -743,6 +798,32 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     p.nout = t.nout;
     for (int i = 0; i < kMaxHighBits; ++i) p.high[i] = t.high[i];
     for (int i = 0; i < kMaxOutBits; ++i) p.outpos[i] = i < (int)t.nout ? t.outpos[i] : 0u;
+    p.tma = t.tma;
+    p.nrest = t.nrest;
+    p.epa = amp_bytes == 16 ? 2 : 1;
+    p.box_bytes = t.box_bytes;
+    for (int i = 0; i < 6; ++i) p.start[i] = t.tma_start[i];
+    for (int i = 0; i < kMaxHighBits; ++i) p.rest_pos[i] = t.rest_pos[i];
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    if (t.tma) {
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) {
+            p.tma = 0;  // no driver entry point: one bulk copy per run
+        } else {
+            cuuint64_t dims[5], strides[4];
+            cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+            for (int d = 0; d < 5; ++d) {
+                dims[d] = t.tma_dim[d];
+                box[d] = t.tma_box[d];
+            }
+            for (int d = 1; d < 5; ++d) strides[d - 1] = t.tma_stride[d];
+            CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, state, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+    }
     const size_t smem = tile_smem_bytes(amp_bytes, (int)t.k);
     const uint64_t cap = (uint64_t)num_sms();
     const int grid = (int)(t.n_tiles < cap ? t.n_tiles : cap);
@@ -752,12 +833,12 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
         e = cudaFuncSetAttribute(tile_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<8><<<grid, kTileThreads + 32, smem, s>>>(p);
+        tile_kernel<8><<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
     } else {
         e = cudaFuncSetAttribute(tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        tile_kernel<16><<<grid, kTileThreads + 32, smem, s>>>(p);
+        tile_kernel<16><<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
     }
     return cudaGetLastError();
 }

@@ -125,10 +125,12 @@ struct TileGeom {
 TileGeom tile_geometry(uint32_t M, const PlanOptions &o)
 {
     TileGeom g;
-    // 64 KiB tiles; runs of 2^l amplitudes of 1 KiB, since each run is one
-    // bulk copy and shorter copies leave the copy engine, not HBM, the limit
-    const uint32_t kdef = o.amp_bytes == 16 ? 12 : 13;
-    const uint32_t ldef = o.amp_bytes == 16 ? 6 : 7;
+    // 128 KiB tiles (one shared-memory stage: more target bits per pass beat
+    // deeper pipelining) whose lowest l bits give runs of 256 bytes for
+    // full-sector, coalesced stores; tiles move in tensor-map boxes, so short
+    // runs do not multiply the number of copies
+    const uint32_t kdef = o.amp_bytes == 16 ? 13 : 14;
+    const uint32_t ldef = o.amp_bytes == 16 ? 4 : 5;
     uint32_t k = o.tile_bits > 0 ? (uint32_t)o.tile_bits : kdef;
     uint32_t l = o.low_bits > 0 ? (uint32_t)o.low_bits : ldef;
     k = std::min<uint32_t>(std::min<uint32_t>(k, kMaxTileBits), M);
@@ -143,6 +145,113 @@ TileGeom tile_geometry(uint32_t M, const PlanOptions &o)
     return g;
 }
 
+// Local bit order of a tile and its tensor-map copy layout.  The tile's bits
+// are the lowest l address bits, extended upwards while the next bit is also
+// a tile bit (one contiguous run, at most 256 copy elements), then up to four
+// further runs of tile bits ("groups", at most 8 bits each, the largest
+// first), then the remaining tile bits.  One tensor copy moves the run and the
+// four groups as a box of a 5-dimensional view of the state (dimension d
+// spans the address bits from the start of group d to the start of group
+// d+1); the remaining bits are enumerated by issuing one copy per value.  The
+// local index of an amplitude in shared memory lists the bits in that order.
+void layout_tile(uint32_t M, uint32_t l, uint64_t high_mask, size_t amp, TilePass *t)
+{
+    const uint32_t epa = amp == 16 ? 2 : 1;          // 8-byte copy elements per amplitude
+    const uint32_t lmax = amp == 16 ? 7 : 8;         // box dimension 0 <= 256 elements
+    uint32_t a0 = l;
+    while (a0 < lmax && a0 < M && ((high_mask >> a0) & 1ull)) ++a0;
+    uint64_t rest = high_mask & ~((1ull << a0) - 1ull);
+    // runs of consecutive tile bits above the low run, split at 8 bits
+    struct Grp { uint32_t start, width; };
+    std::vector<Grp> runs;
+    for (uint64_t h = rest; h;) {
+        const uint32_t b = (uint32_t)__builtin_ctzll(h);
+        uint32_t w = 0;
+        while (w < 8 && ((h >> (b + w)) & 1ull)) ++w;
+        runs.push_back({b, w});
+        h &= ~(((1ull << w) - 1ull) << b);
+    }
+    std::vector<Grp> chosen = runs;
+    std::stable_sort(chosen.begin(), chosen.end(),
+                     [](const Grp &x, const Grp &y) { return x.width > y.width; });
+    if (chosen.size() > 4) chosen.resize(4);
+    std::sort(chosen.begin(), chosen.end(), [](const Grp &x, const Grp &y) { return x.start < y.start; });
+    uint64_t chosen_mask = 0;
+    for (const Grp &c : chosen) chosen_mask |= ((1ull << c.width) - 1ull) << c.start;
+    t->l = a0;
+    t->nh = 0;
+    for (const Grp &c : chosen)
+        for (uint32_t q = 0; q < c.width; ++q) t->high[t->nh++] = c.start + q;
+    t->nrest = 0;
+    for (uint64_t h = rest & ~chosen_mask; h; h &= h - 1) {
+        const uint32_t b = (uint32_t)__builtin_ctzll(h);
+        t->rest_pos[t->nrest++] = b;
+        t->high[t->nh++] = b;
+    }
+    t->k = t->l + t->nh;
+    // tensor-map view: ranges [start[d], start[d+1]) of address bits; a
+    // range wider than 30 bits is split by a dimension with box extent 1
+    // (coordinates are 32-bit signed)
+    std::vector<Grp> dimgrp;  // per dimension >= 1: group start and box width
+    for (const Grp &c : chosen) dimgrp.push_back(c);
+    for (;;) {
+        uint32_t st[6];
+        uint32_t nd = 0;
+        st[nd++] = 0;
+        for (const Grp &c : dimgrp) st[nd++] = c.start;
+        st[nd] = M;
+        int wide = -1;
+        for (uint32_t d = 0; d < nd; ++d)
+            if (st[d + 1] - st[d] + (d == 0 && epa == 2 ? 1 : 0) > 30) wide = (int)d;
+        if (wide < 0 || nd >= 5) break;
+        const uint32_t at = st[wide] + 28;  // the new range starts 28 bits in
+        dimgrp.insert(dimgrp.begin() + wide, Grp{at, 0});
+        std::sort(dimgrp.begin(), dimgrp.end(), [](const Grp &x, const Grp &y) { return x.start < y.start; });
+    }
+    uint32_t start[6];
+    uint32_t nd = 0;
+    start[nd++] = 0;
+    for (const Grp &c : dimgrp) start[nd++] = c.start;
+    const uint32_t ndims = nd;
+    start[nd] = M;
+    bool fits = true;
+    for (uint32_t d = 0; d < ndims; ++d) {
+        const uint32_t width = start[d + 1] - start[d] + (d == 0 && epa == 2 ? 1 : 0);
+        if (width > 30) fits = false;
+    }
+    t->tma = fits ? 1u : 0u;
+    const uint64_t total_bytes = (uint64_t)amp << M;
+    for (uint32_t d = 0; d < 5; ++d) {
+        if (d < ndims) {
+            t->tma_start[d] = start[d];
+            t->tma_dim[d] = (1ull << (start[d + 1] - start[d])) * (d == 0 ? epa : 1);
+            t->tma_stride[d] = d == 0 ? amp : (uint64_t)amp << start[d];
+            t->tma_box[d] = d == 0 ? (epa << a0) : (1u << dimgrp[d - 1].width);
+        } else {  // unused dimensions: extent 1
+            t->tma_start[d] = M;
+            t->tma_dim[d] = 1;
+            t->tma_stride[d] = total_bytes;
+            t->tma_box[d] = 1;
+        }
+    }
+    t->tma_start[5] = M;
+    t->tma_ndims = ndims;
+    t->box_bytes = (uint32_t)(amp << (t->k - t->nrest));
+    // Copy-engine rules, checked here so that no copy can break them: every
+    // box lands on a 128-byte boundary of shared memory (stage buffers are
+    // whole tiles), box extents are at most 256 elements, the first
+    // coordinate is a multiple of 16 bytes (the low a0 >= 1 bits of a box
+    // origin are zero), and each box lies inside its dimension.
+    const uint64_t tile_bytes = (uint64_t)amp << t->k;
+    bool ok = t->tma && t->box_bytes % 128 == 0 && tile_bytes % 128 == 0 && a0 >= 1;
+    for (uint32_t d = 0; d < 5 && ok; ++d) {
+        ok = t->tma_box[d] >= 1 && t->tma_box[d] <= 256 && t->tma_box[d] <= t->tma_dim[d] &&
+             t->tma_dim[d] % t->tma_box[d] == 0 && t->tma_stride[d] % (d == 0 ? 8 : 16) == 0;
+    }
+    if (ok && ((uint64_t)t->tma_box[0] * 8) % 16 != 0) ok = false;
+    t->tma = ok ? 1u : 0u;
+}
+
 // Build one tile pass for the given step indices and high-bit set.
 void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &seg,
                uint64_t high_mask, const TileGeom &g, const PlanOptions &o, Plan *plan)
@@ -154,17 +263,11 @@ void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &
     uint32_t want = std::min<uint32_t>(g.nh_max, M - g.l);
     for (uint32_t b = g.l; b < M && (uint32_t)popcount64(high_mask) < want; ++b)
         high_mask |= 1ull << b;
-    t.l = g.l;
-    t.nh = 0;
+    layout_tile(M, g.l, high_mask, o.amp_bytes, &t);
     int8_t g2l[64];
     for (int b = 0; b < 64; ++b) g2l[b] = -1;
-    for (uint32_t b = 0; b < g.l; ++b) g2l[b] = (int8_t)b;
-    for (uint64_t h = high_mask; h; h &= h - 1) {
-        const uint32_t b = (uint32_t)__builtin_ctzll(h);
-        g2l[b] = (int8_t)(g.l + t.nh);
-        t.high[t.nh++] = b;
-    }
-    t.k = t.l + t.nh;
+    for (uint32_t b = 0; b < t.l; ++b) g2l[b] = (int8_t)b;
+    for (uint32_t q = 0; q < t.nh; ++q) g2l[t.high[q]] = (int8_t)(t.l + q);
     t.n_tiles = 1ull << (M - t.k);
     t.step_off = (uint32_t)plan->tile_steps.size();
     t.nsteps = (uint32_t)seg.size();

@@ -69,6 +69,15 @@ struct SweepParams {
 struct TilePass {
     uint32_t k, l, nh;  // tile width, contiguous low bits, high bits
     uint32_t high[kMaxHighBits];
+    uint32_t tma;       // 1: tensor-map copies (else one bulk copy per run)
+    uint32_t tma_ndims; // dimensions of the view that carry tile bits
+    uint32_t tma_start[6];    // first address bit of each dimension's range
+    uint64_t tma_dim[5];      // extents in 8-byte elements
+    uint64_t tma_stride[5];   // byte strides (dimension 0: element size)
+    uint32_t tma_box[5];      // box extents
+    uint32_t box_bytes;       // bytes moved by one copy
+    uint32_t nrest;           // tile bits enumerated by separate copies
+    uint32_t rest_pos[kMaxHighBits];
     uint32_t nout;      // address bits outside the tile (M - k)
     uint32_t outpos[40];  // their positions, in tile-id bit order: bits that
                           // are controls of some step come last (slowest)
