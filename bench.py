@@ -377,6 +377,12 @@ def run_ours(args, rank, ws, local):
                    nst, L, M, secs)}
 
     launches = len(passes)  # every pass kernel and probabilities kernel in the timed region
+
+    # ---- batched vs one launch per circuit (part of the metric) ----------------
+    batch = None
+    if not args.no_batch:
+        sim.close()
+        batch = batch_speedup(args.batch_compare, "cnot", 10, 3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -403,10 +409,49 @@ def run_ours(args, rank, ws, local):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     sim.close()
     return 0
+
+
+def batch_speedup(n: int, mix: str, steps: int, warmup: int):
+    """Time one batch run (graph of persistent launches) against one plain
+    launch per circuit pass on n circuits of the batched workload; returns a
+    dict for the JSON line.  Used by the default benchmark for the
+    batched-vs-plain part of the metric."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Batch
+    specs = W.batch_specs(n, seed=4, mix=mix)
+    dtype = np.dtype(np.complex64)
+    b = Batch([(s["M"], s["steps"]) for s in specs], dtype)
+    for i, sp in enumerate(specs):
+        b.load_state(i, W.random_state(sp["M"], dtype, sp["state_seed"]))
+    info = b.info()
+    stream = torch.cuda.ExternalStream(info["stream"])
+
+    def timed(fn, k):
+        for _ in range(warmup):
+            fn()
+        b.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        b.synchronize()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_b = timed(b.run, steps)
+    ms_p = timed(b.run_plain, steps)
+    b.close()
+    return {"circuits": n, "mix": mix, "amplitude_steps_per_run": info["amplitude_steps"],
+            "batched_ms": ms_b, "plain_ms": ms_p, "batched_over_plain": ms_p / ms_b,
+            "batched_value": info["amplitude_steps"] / (ms_b * 1e-3),
+            "plain_value": info["amplitude_steps"] / (ms_p * 1e-3)}
 
 
 def run_batch(args, rank, ws, local):
@@ -581,6 +626,10 @@ def main():
     ap.add_argument("--no-jit", dest="jit", action="store_false",
                     help="use the general bit-sliced gather instead of compiled kernels")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-vs-plain comparison of the default run")
+    ap.add_argument("--batch-compare", type=int, default=1024,
+                    help="circuits in the default run's batched-vs-plain comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
