@@ -69,6 +69,8 @@ def workload(name: str):
         return W.config_cnot(28)
     if name == "adder_m28":  # 2 GiB in-place adder: the small case for tile-kernel captures
         return W.config_adder(13)
+    if name == "parity_m32":  # Sec. 4 example, input generated on the device (App. 1)
+        return W.config_parity(32)
     raise SystemExit("unknown workload " + name)
 
 
@@ -270,10 +272,20 @@ def run_ours(args, rank, ws, local):
     strategy = strategy_for(args.workload)
     tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
 
-    # seeded state in pinned host memory (also the e2e input buffer)
-    h_in_t = torch.empty(n, dtype=tdt, pin_memory=True)
-    h_in = h_in_t.numpy()
-    W.random_state(M, dtype, cfg["state_seed"], out=h_in)
+    # seeded state in pinned host memory (also the e2e input buffer), or the
+    # qubits of a product-state input generated on the device (App. 1)
+    qubits = cfg.get("qubits")
+    h_in = None
+    if qubits is None:
+        h_in_t = torch.empty(n, dtype=tdt, pin_memory=True)
+        h_in = h_in_t.numpy()
+        W.random_state(M, dtype, cfg["state_seed"], out=h_in)
+
+    def load_input():
+        if qubits is None:
+            sim.load_state(h_in)
+        else:
+            sim.load_product_state(qubits)
 
     sim = Simulator(M, dtype, scratch=(strategy != "inplace"))
     sim.set_strategy(strategy, args.tile_bits, args.low_bits)
@@ -291,7 +303,7 @@ def run_ours(args, rank, ws, local):
         sim.probabilities_device(probs.data_ptr())
 
     # ---- device-resident timing ------------------------------------------------
-    sim.load_state(h_in)
+    load_input()
     for _ in range(args.warmup):
         step()
     sim.synchronize()
@@ -340,36 +352,70 @@ def run_ours(args, rank, ws, local):
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
-        h_out_t = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        h_out = h_out_t.numpy()
-        h2d = n * amp
+        # Each step copies its state in from pinned host memory, applies the
+        # circuit and copies its FP64 probabilities out, all through the C ABI.
+        # Two contexts on two streams alternate steps, so one step's copies
+        # overlap the other's kernels (each context waits for its previous
+        # step before reusing its buffers).
+        h2d = n * amp if qubits is None else qubits.nbytes
         d2h = n * 8
+        s2 = torch.cuda.Stream()
+        with torch.cuda.stream(s2):
+            sim2 = Simulator(M, dtype, scratch=(strategy != "inplace"))
+        sim2.set_strategy(strategy, args.tile_bits, args.low_bits)
+        sim2.set_canonicalize(False)
+        if jit_ms is not None:
+            sim2.set_jit(True)
+        sims = (sim, sim2)
+        streams = (stream, s2)
+        outs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(2)]
 
-        def e2e_step():
-            sim.load_state(h_in)
-            sim.apply(steps)
-            sim.probabilities(out=h_out)
+        loaded = [torch.cuda.Event() for _ in range(2)]
 
-        e2e_step()
+        def e2e_step(i):
+            c = i & 1
+            sm = sims[c]
+            if i >= 2:
+                sm.synchronize()  # this context's previous step is done
+            if i >= 1:  # copies in go one after the other over the host link
+                streams[c].wait_event(loaded[1 - c])
+            if qubits is None:
+                sm.load_state_async(h_in)
+            else:
+                sm.load_product_state(qubits)
+            loaded[c].record(streams[c])
+            sm.apply(steps)
+            sm.probabilities_async(outs[c].numpy())
+
+        for i in range(2):  # warm both contexts
+            e2e_step(i)
+        for sm in sims:
+            sm.synchronize()
         torch.cuda.synchronize()
         barrier(ws)
         f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        ke = max(1, args.steps)
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ke = max(2, args.steps)
         f0.record(stream)
-        for _ in range(ke):
-            e2e_step()
-        f1.record(stream)
+        s2.wait_event(f0)
+        for i in range(ke):
+            e2e_step(i)
+        for sm in sims:
+            sm.synchronize()
+        for j in range(2):
+            ends[j].record(streams[j])
         torch.cuda.synchronize()
-        ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws)
+        ms_e2e = max_over_ranks(max(f0.elapsed_time(e) for e in ends), ws)
         e2e = {"value": ws * n * L * ke / (ms_e2e * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": ms_e2e / ke}
-        del h_out
+               "ms_per_step": ms_e2e / ke,
+               "pipelining": "two contexts on two streams alternate steps; copies in are serialised"}
+        sim2.close()
+        del outs
 
     # ---- CPU baseline: the oracle on a bounded prefix (rank 0, N=1) -----------
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and h_in is not None:
         nst = min(L, args.cpu_steps)
         rate, secs = oracle_sample_rate(cfg, nst, h_in)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -610,7 +656,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28",
+    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
                              "batch_cnot", "batch_mixed", "serve"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")

@@ -120,9 +120,26 @@ void qsim_destroy(qsim_ctx *ctx);
  * n_amps must equal 2^M.  Synchronous with respect to host_amps. */
 int qsim_load_state(qsim_ctx *ctx, const void *host_amps, size_t n_amps);
 
+/* Set the state to the product state of App. 1 without sending 2^M
+ * amplitudes: k1(i) = product over bits b of q_b(bit b of i), where qubits
+ * holds 4*M doubles (re q_b(0), im q_b(0), re q_b(1), im q_b(1)) for b = 0
+ * (the paper's a(1)) to M-1.  Computed on the device in FP64 as the product
+ * of the factors of the bits above the lowest min(M, 10) times the product
+ * of the factors of those lowest bits, each partial product taken from the
+ * most significant bit down, every real product and sum rounded separately;
+ * complex64 states are rounded once at the end.  Queued on the context's
+ * stream; qubits is copied during the call. */
+int qsim_load_product_state(qsim_ctx *ctx, const double *qubits);
+
 /* Copy the state (k2) to host memory; n_amps must equal 2^M.  Waits for all
  * work queued on the context and reports device-side errors. */
 int qsim_read_state(qsim_ctx *ctx, void *host_amps, size_t n_amps);
+
+/* As qsim_load_state, but queued on the context's stream without waiting:
+ * host_amps must stay valid and unchanged until the next qsim_synchronize
+ * (pinned memory makes the copy asynchronous).  Lets a caller overlap the
+ * copy-in of one state with work on another context. */
+int qsim_load_state_async(qsim_ctx *ctx, const void *host_amps, size_t n_amps);
 
 /* Device pointer of the buffer that holds the current state. */
 void *qsim_state_device(qsim_ctx *ctx);
@@ -136,6 +153,15 @@ void *qsim_state_device(qsim_ctx *ctx);
  * returns without waiting for it; errors of queued kernels surface at the
  * next qsim_synchronize / qsim_read_state / qsim_probabilities. */
 int qsim_apply_circuit(qsim_ctx *ctx, const qsim_step *steps, size_t L);
+
+/* The row array of the circuit's product (Sec. 2h) -- the information about
+ * the unitary matrix that the paper's conclusions propose to keep for design
+ * automation: d_rows[i] = x(i) with k2(i) = k1(x(i)) for k2 = U_L ... U_1 k1,
+ * for all 2^M rows, written to device memory (2^M uint64, 8-byte aligned) on
+ * the context's stream.  The state is not touched.  Every step is used (no
+ * cancellation); QSIM_EINVAL for an invalid step or one with more than eight
+ * controls. */
+int qsim_row_array(qsim_ctx *ctx, const qsim_step *steps, size_t L, uint64_t *d_rows);
 
 /* Force a strategy for subsequent qsim_apply_circuit calls (tests and
  * tuning).  tile_bits: total tile width k (0 = default), low_bits: how many
@@ -181,7 +207,8 @@ int qsim_set_profiling(qsim_ctx *ctx, int enable);
 int qsim_get_pass_times(qsim_ctx *ctx, double *ms, uint32_t *kinds, double *alg_bytes,
                         size_t cap, size_t *n_out);
 
-/* Wait for queued work; returns QSIM_ETIMEOUT / QSIM_ECUDA if a kernel failed. */
+/* Wait for queued work (kernels and probability copies); returns
+ * QSIM_ETIMEOUT / QSIM_ECUDA if a kernel failed. */
 int qsim_synchronize(qsim_ctx *ctx);
 
 /* ---- post-processing ----------------------------------------------------- */
@@ -191,6 +218,12 @@ int qsim_synchronize(qsim_ctx *ctx);
  * 2^M.  norm_out (may be NULL) receives sum_i p(i), reduced in FP64 on the
  * device.  Synchronous. */
 int qsim_probabilities(qsim_ctx *ctx, double *host_probs, size_t n, double *norm_out);
+
+/* As qsim_probabilities without the norm, queued without waiting: chunks of
+ * probabilities are computed on the context's stream and copied to
+ * host_probs (2^M doubles, valid until the next qsim_synchronize) on a second
+ * stream of the context.  qsim_synchronize waits for both. */
+int qsim_probabilities_async(qsim_ctx *ctx, double *host_probs, size_t n);
 
 /* As qsim_probabilities, into device memory d_probs (2^M doubles, 8-byte
  * aligned), queued on the context's stream.  norm_out (may be NULL) is a

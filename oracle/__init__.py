@@ -75,6 +75,8 @@ def _load():
         lib.oracle_apply_circuit.restype = i32
         lib.oracle_source_rows.argtypes = [u32, p, sz, p, sz, p]
         lib.oracle_source_rows.restype = i32
+        lib.oracle_product_state.argtypes = [u32, p, p]
+        lib.oracle_product_state.restype = i32
         lib.oracle_probabilities.argtypes = [p, sz, p]
         lib.oracle_probabilities.restype = None
         lib.oracle_sum.argtypes = [p, sz]
@@ -167,6 +169,16 @@ def sample_outputs(M: int, k1_lookup, steps, rows) -> np.ndarray:
     """k2 at selected rows: k1_lookup(source rows) gathers the input values."""
     src = source_rows(M, steps, rows)
     return np.asarray(k1_lookup(src.astype(np.int64)), dtype=np.complex128)
+
+
+def product_state(M: int, qubits) -> np.ndarray:
+    """k1 from M qubits (App. 1): qubits[b] = (q_{b+1}(0), q_{b+1}(1))."""
+    q = np.ascontiguousarray(qubits, dtype=np.complex128)
+    if q.shape != (M, 2):
+        raise ValueError("qubits must be a complex (M, 2) array")
+    k = np.empty(1 << M, dtype=np.complex128)
+    _check(_load().oracle_product_state(M, _ptr(q), _ptr(k)), "product_state")
+    return k
 
 
 def probabilities(k: np.ndarray) -> np.ndarray:

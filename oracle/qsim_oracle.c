@@ -211,6 +211,32 @@ int oracle_source_rows(uint32_t M, const ostep *steps, size_t L,
 }
 
 /*
+ * Input state generated from M qubits (App. 1): k1 is the Kronecker product
+ * q_M (x) ... (x) q_2 (x) q_1, so k1(i) is the product of the component of
+ * each qubit picked by the matching bit of i -- e.g. k1(5) = q3(1) q2(0) q1(1).
+ * The factors are multiplied in that printed order, most significant qubit
+ * first; each complex product is (ac - bd) + (ad + bc)i with every real
+ * product and sum rounded separately.  q[2*b + v] is qubit b+1's component v.
+ */
+int oracle_product_state(uint32_t M, const ocplx *q, ocplx *k)
+{
+    if (M < 1 || M > 30) return ORACLE_EINVAL;
+    const uint64_t n = 1ull << M;
+    for (uint64_t i = 0; i < n; ++i) {
+        ocplx acc = q[2 * (M - 1) + ((i >> (M - 1)) & 1u)];
+        for (int b = (int)M - 2; b >= 0; --b) {
+            const ocplx f = q[2 * b + ((i >> b) & 1u)];
+            const double re = acc.re * f.re - acc.im * f.im;
+            const double im = acc.re * f.im + acc.im * f.re;
+            acc.re = re;
+            acc.im = im;
+        }
+        k[i] = acc;
+    }
+    return ORACLE_OK;
+}
+
+/*
  * Basis-state probabilities |k(i)|^2 = re^2 + im^2 in FP64 (the state's
  * post-processing, Sec. 2b; amplitudes of arbitrary magnitude and phase,
  * Sec. 1).  Two products and one sum, no fused multiply-add.

@@ -46,7 +46,8 @@ EXPORTS = (
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
-    "qsim_probabilities_noalloc", "qsim_batch_create", "qsim_batch_destroy",
+    "qsim_probabilities_noalloc", "qsim_load_product_state", "qsim_row_array",
+    "qsim_load_state_async", "qsim_probabilities_async", "qsim_batch_create", "qsim_batch_destroy",
     "qsim_batch_load_state", "qsim_batch_read_state", "qsim_batch_state_device", "qsim_batch_run",
     "qsim_batch_run_plain", "qsim_batch_synchronize", "qsim_batch_info", "qsim_server_create",
     "qsim_server_submit", "qsim_server_poll", "qsim_server_release", "qsim_server_wait_all",
@@ -132,6 +133,10 @@ def load() -> ctypes.CDLL:
             "qsim_probabilities_device": ([p, p, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_plan_circuit": ([u32, i, p, sz, i, i, i, i, ctypes.POINTER(PlanStats), p, p, p, sz], i),
             "qsim_probabilities_noalloc": ([p, u32, i, p, p, p], i),
+            "qsim_load_product_state": ([p, p], i),
+            "qsim_row_array": ([p, p, sz, p], i),
+            "qsim_load_state_async": ([p, p, sz], i),
+            "qsim_probabilities_async": ([p, p, sz], i),
             "qsim_batch_create": ([sz, p, i, p, p, pp], i),
             "qsim_batch_destroy": ([p], None),
             "qsim_batch_load_state": ([p, sz, p, sz], i),
@@ -269,6 +274,27 @@ class Simulator:
             raise QsimError(QSIM_EINVAL, "state must have 2^M amplitudes")
         _check(self._lib.qsim_load_state(self._ctx, _ptr(a), self.n))
 
+    def load_state_async(self, k1: np.ndarray):
+        """Queue the copy-in of k1 (keep it alive and unchanged, ideally pinned,
+        until synchronize())."""
+        if k1.dtype != self.dtype or k1.shape != (self.n,) or not k1.flags.c_contiguous:
+            raise QsimError(QSIM_EINVAL, "state must be a contiguous array of 2^M amplitudes")
+        _check(self._lib.qsim_load_state_async(self._ctx, _ptr(k1), self.n))
+
+    def probabilities_async(self, out: np.ndarray):
+        """Queue probabilities into out (2^M float64, kept alive until synchronize())."""
+        if out.dtype != np.float64 or out.shape != (self.n,) or not out.flags.c_contiguous:
+            raise QsimError(QSIM_EINVAL, "out must be a contiguous float64 array of 2^M entries")
+        _check(self._lib.qsim_probabilities_async(self._ctx, _ptr(out), self.n))
+
+    def load_product_state(self, qubits: np.ndarray):
+        """Product state of App. 1 from M qubit pairs: qubits[b] = (q_b(0), q_b(1))
+        as a complex (M, 2) array; b = 0 is the paper's a(1)."""
+        q = np.ascontiguousarray(qubits, dtype=np.complex128)
+        if q.shape != (self.M, 2):
+            raise QsimError(QSIM_EINVAL, "qubits must be a complex (M, 2) array")
+        _check(self._lib.qsim_load_product_state(self._ctx, _ptr(q)))
+
     def read_state(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:
             out = np.empty(self.n, dtype=self.dtype)
@@ -315,6 +341,12 @@ class Simulator:
         _check(self._lib.qsim_get_pass_times(self._ctx, _ptr(ms), _ptr(kinds), _ptr(by), k,
                                              ctypes.byref(n)))
         return [(KERNEL[int(kinds[i])], float(ms[i]), float(by[i])) for i in range(k)]
+
+    def row_array(self, steps, out_ptr: int):
+        """x(i) for every row (Sec. 2h product) into device memory at out_ptr
+        (2^M uint64)."""
+        s = as_steps(steps)
+        _check(self._lib.qsim_row_array(self._ctx, _ptr(s), len(s), ctypes.c_void_p(out_ptr)))
 
     def plan_stats(self) -> dict:
         st = PlanStats()

@@ -157,6 +157,7 @@ struct TileKParams {
     uint32_t high[kMaxHighBits];
     uint32_t outpos[kMaxOutBits];  // global bit of tile-id bit q
     uint32_t tma, nrest, epa, box_bytes;
+    uint32_t affine;               // every step has at most one control
     uint32_t start[6];             // tensor view: first address bit of each dimension
     uint32_t rest_pos[kMaxHighBits];
 };
@@ -321,6 +322,8 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 
     // ---------------- consumer warps ----------------
     const uint32_t lmask = (1u << p.l) - 1u;
+    bool have_perm = false;  // perm holds the table of an earlier tile
+    uint32_t c0 = 0, delta = 0;  // affine passes: image of 0 in that table, shift now
     A *st = reinterpret_cast<A *>(p.state);
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
@@ -330,7 +333,16 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
         }
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
-        if (!meta[s].same) {
+        if (!meta[s].same && p.affine && have_perm) {
+            // NOT/CNOT segment: every tile's map is A j ^ c(tile) with the same
+            // A, so the table of the first tile is reused with c(tile) ^ c(first)
+            uint32_t c = 0;
+            for (int q = (int)p.nsteps - 1; q >= 0; --q) {
+                if (!((meta[s].mask[q >> 5] >> (q & 31)) & 1u)) continue;
+                if ((c & steps_sm[q].cl) == steps_sm[q].pl) c ^= steps_sm[q].tmask;
+            }
+            delta = c ^ c0;
+        } else if (!meta[s].same) {
             consumer_sync();  // every consumer is done with the previous table
             for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 8) {
                 uint32_t src[8];
@@ -349,6 +361,14 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                     if (j < tile_amps) perm[j] = (uint16_t)src[e];
                 }
             }
+            // the table's own image of local index 0 (every thread evaluates it)
+            c0 = 0;
+            for (int q = (int)p.nsteps - 1; q >= 0; --q) {
+                if (!((meta[s].mask[q >> 5] >> (q & 31)) & 1u)) continue;
+                if ((c0 & steps_sm[q].cl) == steps_sm[q].pl) c0 ^= steps_sm[q].tmask;
+            }
+            delta = 0;
+            have_perm = true;
             consumer_sync();  // the new table is complete
         }
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const uint32_t j = j0 + tid + e * kTileThreads;
-                if (j < tile_amps) v[e] = buf[perm[j]];
+                if (j < tile_amps) v[e] = buf[perm[j] ^ delta];
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -468,8 +488,10 @@ __host__ __device__ constexpr size_t sliced_smem_for(uint32_t M)
 }
 
 // One CTA: outputs [cbase, cbase + kSlicedOutputs) of a bit-sliced pass.
-// Every thread of the CTA must call it (it synchronises the CTA).
-template <int B, bool WIDE>
+// Every thread of the CTA must call it (it synchronises the CTA).  With MAP
+// the source rows x(i) themselves are written to out (64-bit integers, the
+// row array of the product, Sec. 2h) instead of gathering amplitudes.
+template <int B, bool WIDE, bool MAP = false>
 __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out, uint32_t M,
                              uint64_t n, const SlicedStep *__restrict__ steps, uint32_t nsteps,
                              uint64_t cbase, unsigned char *smem)
@@ -560,11 +582,17 @@ __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out
                 o[u] = wbase + (uint64_t)e * 64 + 32 * half + lane;
                 uint64_t x = tab[e * 33 + lane];
                 if (WIDE) x |= (uint64_t)hi[e * 33 + lane] << 32;
-                if (o[u] < n) v[u] = __ldg(&src[x]);
+                if (MAP) {
+                    if (o[u] < n) reinterpret_cast<uint64_t *>(out)[o[u]] = x;
+                } else if (o[u] < n) {
+                    v[u] = __ldg(&src[x]);
+                }
             }
+            if (!MAP) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (o[u] < n) dst[o[u]] = v[u];
+                for (int u = 0; u < 8; ++u)
+                    if (o[u] < n) dst[o[u]] = v[u];
+            }
         }
     }
     __syncwarp();
@@ -580,6 +608,21 @@ __global__ void __launch_bounds__(kThreads, 2) gather_sliced_kernel(
     // the loop bound is uniform over the CTA, so the barriers inside are safe
     for (uint64_t cbase = (uint64_t)blockIdx.x * kSlicedOutputs; cbase < n; cbase += per_iter)
         sliced_chunk<B, WIDE>(in, out, M, n, steps, nsteps, cbase, smem);
+}
+
+// Row array of the product of a step list: rows[i] = x(i) for every output
+// row i (the array the paper keeps, Sec. 2h), evaluated bit-sliced.
+template <bool WIDE>
+__global__ void __launch_bounds__(kThreads, 2) row_array_kernel(uint64_t *__restrict__ rows,
+                                                                 uint32_t M, uint64_t n,
+                                                                 const SlicedStep *__restrict__ steps,
+                                                                 uint32_t nsteps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint64_t per_iter = (uint64_t)gridDim.x * kSlicedOutputs;
+    for (uint64_t cbase = (uint64_t)blockIdx.x * kSlicedOutputs; cbase < n; cbase += per_iter)
+        sliced_chunk<8, WIDE, true>(nullptr, reinterpret_cast<char *>(rows), M, n, steps, nsteps,
+                                    cbase, smem);
 }
 
 // Sweep of pair indices [q0, q1) of one step (in place).
@@ -648,6 +691,62 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__rest
 // ============================================================================
 // FP64 probabilities and norm
 // ============================================================================
+
+// ============================================================================
+// product-state input (App. 1): k1(i) = product over qubits of q_b(bit b of i)
+// ============================================================================
+
+// Complex product with each real product and sum rounded separately.
+__device__ __forceinline__ double2 cmul_rn(double2 a, double2 b)
+{
+    return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
+                        __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+
+// Product of the factors of bits [lo, hi) of index i, most significant
+// first; q holds (q_b(0), q_b(1)) for each bit b.
+__device__ __forceinline__ double2 partial_product(const double2 *q, uint64_t i, int lo, int hi)
+{
+    double2 acc = q[2 * (hi - 1) + ((i >> (hi - 1)) & 1ull)];
+    for (int b = hi - 2; b >= lo; --b) acc = cmul_rn(acc, q[2 * b + ((i >> b) & 1ull)]);
+    return acc;
+}
+
+constexpr int kProductLowBits = 10;  // table of low-bit partial products in shared memory
+
+// k1(i) = (product over the high bits) x (product over the low h bits): the
+// low-bit partial products of the whole state fit one 2^h table, and each
+// CTA computes the high-bit partial product of its range once.
+template <int B>
+__global__ void __launch_bounds__(kThreads) product_state_kernel(char *__restrict__ state,
+                                                                 const double *__restrict__ qubits,
+                                                                 uint32_t M, uint64_t n)
+{
+    __shared__ double2 q[2 * QSIM_MAX_QUBITS];
+    __shared__ double2 lo_tab[1 << kProductLowBits];
+    __shared__ double2 hi_val;
+    const int h = M < (uint32_t)kProductLowBits ? (int)M : kProductLowBits;
+    for (uint32_t j = threadIdx.x; j < 2 * M; j += kThreads)
+        q[j] = make_double2(qubits[2 * j], qubits[2 * j + 1]);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < (1u << h); j += kThreads) lo_tab[j] = partial_product(q, j, 0, h);
+    // each CTA covers whole runs of 2^h consecutive indices (one high value each)
+    const uint64_t runs = n >> h;
+    for (uint64_t r = blockIdx.x; r < runs; r += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) hi_val = (int)M > h ? partial_product(q, r << h, h, (int)M) : make_double2(1.0, 0.0);
+        __syncthreads();
+        const double2 hv = hi_val;
+        for (uint32_t j = threadIdx.x; j < (1u << h); j += kThreads) {
+            const double2 v = (int)M > h ? cmul_rn(hv, lo_tab[j]) : lo_tab[j];
+            const uint64_t i = (r << h) | j;
+            if (B == 16)
+                reinterpret_cast<double2 *>(state)[i] = v;
+            else
+                reinterpret_cast<float2 *>(state)[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+        }
+    }
+}
 
 constexpr int kProbBlocks = 1024;
 
@@ -799,6 +898,7 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     for (int i = 0; i < kMaxHighBits; ++i) p.high[i] = t.high[i];
     for (int i = 0; i < kMaxOutBits; ++i) p.outpos[i] = i < (int)t.nout ? t.outpos[i] : 0u;
     p.tma = t.tma;
+    p.affine = t.affine;
     p.nrest = t.nrest;
     p.epa = amp_bytes == 16 ? 2 : 1;
     p.box_bytes = t.box_bytes;
@@ -962,6 +1062,42 @@ int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, cons
                     : launch_batch_t<8, false>(d_passes, d_items, n_items, d_counter, smem, s);
     return wide ? launch_batch_t<16, true>(d_passes, d_items, n_items, d_counter, smem, s)
                 : launch_batch_t<16, false>(d_passes, d_items, n_items, d_counter, smem, s);
+}
+
+int launch_product_state(void *state, int amp_bytes, uint32_t M, const double *d_qubits, void *stream)
+{
+    const uint64_t n = 1ull << M;
+    const int h = M < (uint32_t)kProductLowBits ? (int)M : kProductLowBits;
+    const uint64_t runs = n >> h;
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    const int grid = (int)(runs < cap ? runs : cap);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (amp_bytes == 8)
+        product_state_kernel<8><<<grid, kThreads, 0, s>>>(static_cast<char *>(state), d_qubits, M, n);
+    else
+        product_state_kernel<16><<<grid, kThreads, 0, s>>>(static_cast<char *>(state), d_qubits, M, n);
+    return cudaGetLastError();
+}
+
+int launch_row_array(uint64_t *d_rows, uint32_t M, const SlicedStep *d_steps, uint32_t nsteps,
+                     void *stream)
+{
+    const uint64_t n = 1ull << M;
+    const size_t smem = sliced_smem_for(M);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t chunks = (n + kSlicedOutputs - 1) / kSlicedOutputs;
+    const uint64_t cap = (uint64_t)num_sms() * 2;
+    const int grid = (int)(chunks < cap ? chunks : cap);
+    cudaError_t e;
+    if (M > 32) {
+        e = cudaFuncSetAttribute(row_array_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) row_array_kernel<true><<<grid, kThreads, smem, s>>>(d_rows, M, n, d_steps, nsteps);
+    } else {
+        e = cudaFuncSetAttribute(row_array_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) row_array_kernel<false><<<grid, kThreads, smem, s>>>(d_rows, M, n, d_steps, nsteps);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 }  // namespace qsim

@@ -288,6 +288,9 @@ void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &
         plan->tile_steps.push_back(ts);
     }
     t.all_local = all_local ? 1u : 0u;
+    bool affine = true;
+    for (uint64_t idx : seg) affine = affine && popcount64(steps[idx].ctrl_mask) <= 1;
+    t.affine = affine ? 1u : 0u;
     // tile-id bit order: out-of-tile bits that no step controls vary fastest,
     // control bits slowest (runs of tiles with the same active steps)
     uint64_t ctl_out = 0;
@@ -578,6 +581,26 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
         }
     }
     *plan = std::move(tp);
+    return QSIM_OK;
+}
+
+int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<SlicedStep> *out,
+                    std::string *msg)
+{
+    int rc = validate_steps(M, steps, L, msg);
+    if (rc != QSIM_OK) return rc;
+    for (size_t i = 0; i < L; ++i)
+        if (popcount64(steps[i].ctrl_mask) > kSlicedMaxControls) {
+            if (msg) *msg = "step " + std::to_string(i) + " has more than " +
+                            std::to_string(kSlicedMaxControls) + " controls";
+            return QSIM_EINVAL;
+        }
+    Plan tmp;
+    std::vector<uint64_t> seg(L);
+    for (size_t i = 0; i < L; ++i) seg[i] = i;
+    PlanOptions o;
+    emit_sliced(M, steps, seg, o, &tmp);
+    *out = std::move(tmp.sliced_steps);
     return QSIM_OK;
 }
 

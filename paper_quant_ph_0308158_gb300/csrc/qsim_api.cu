@@ -3,6 +3,7 @@
 // kernels.cu and the planner in planner.cpp.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -64,7 +65,9 @@ struct qsim_ctx {
     bool plan_ev_pending = false;
     double *d_partials = nullptr;
     double *d_norms = nullptr;
-    double *d_probs_chunk = nullptr;
+    double *d_probs_chunk[2] = {nullptr, nullptr};  // double buffer for host probabilities
+    cudaStream_t copy_stream = nullptr;               // device-to-host copies of those chunks
+    cudaEvent_t chunk_ready[2] = {nullptr, nullptr}, chunk_copied[2] = {nullptr, nullptr};
     PlanOptions opts;
     qsim_plan_stats stats{};
     // tracing: events around each pass of the last apply
@@ -102,7 +105,12 @@ void ctx_free(qsim_ctx *c)
     if (c->plan_ev) cudaEventDestroy(c->plan_ev);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_norms) cudaFree(c->d_norms);
-    if (c->d_probs_chunk) cudaFree(c->d_probs_chunk);
+    for (int i = 0; i < 2; ++i) {
+        if (c->d_probs_chunk[i]) cudaFree(c->d_probs_chunk[i]);
+        if (c->chunk_ready[i]) cudaEventDestroy(c->chunk_ready[i]);
+        if (c->chunk_copied[i]) cudaEventDestroy(c->chunk_copied[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -273,6 +281,58 @@ int qsim_load_state(qsim_ctx *c, const void *host, size_t n_amps)
     return QSIM_OK;
 }
 
+int qsim_load_state_async(qsim_ctx *c, const void *host, size_t n_amps)
+{
+    if (!c || !host) return fail(QSIM_EINVAL, "NULL argument");
+    if (n_amps != c->n) return fail(QSIM_EINVAL, "n_amps must equal 2^M");
+    QSIM_CUDA(cudaMemcpyAsync(c->buf[c->cur], host, c->amp * c->n, cudaMemcpyHostToDevice, c->stream),
+              "cudaMemcpy(load state)");
+    return QSIM_OK;
+}
+
+int qsim_load_product_state(qsim_ctx *c, const double *qubits)
+{
+    if (!c || !qubits) return fail(QSIM_EINVAL, "NULL argument");
+    const size_t bytes = sizeof(double) * 4 * c->M;
+    // the qubit table rides in the plan-table staging buffers
+    int rc = ensure_plan_buffers(c, bytes);
+    if (rc != QSIM_OK) return rc;
+    std::memcpy(c->h_plan, qubits, bytes);
+    QSIM_CUDA(cudaMemcpyAsync(c->d_plan, c->h_plan, bytes, cudaMemcpyHostToDevice, c->stream),
+              "cudaMemcpy(qubits)");
+    QSIM_CUDA(cudaEventRecord(c->plan_ev, c->stream), "cudaEventRecord");
+    c->plan_ev_pending = true;
+    const int e = launch_product_state(c->buf[c->cur], (int)c->amp, c->M,
+                                       reinterpret_cast<const double *>(c->d_plan), c->stream);
+    if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "product-state launch");
+    return QSIM_OK;
+}
+
+int qsim_row_array(qsim_ctx *c, const qsim_step *steps, size_t L, uint64_t *d_rows)
+{
+    if (!c || !d_rows) return fail(QSIM_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(d_rows) & 7u) return fail(QSIM_EINVAL, "d_rows misaligned");
+    std::vector<SlicedStep> sl;
+    std::string msg;
+    int rc = sliced_steps_of(c->M, steps, L, &sl, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    const size_t bytes = std::max<size_t>(16, sl.size() * sizeof(SlicedStep));
+    rc = ensure_plan_buffers(c, bytes);
+    if (rc != QSIM_OK) return rc;
+    if (!sl.empty()) {
+        std::memcpy(c->h_plan, sl.data(), sl.size() * sizeof(SlicedStep));
+        QSIM_CUDA(cudaMemcpyAsync(c->d_plan, c->h_plan, sl.size() * sizeof(SlicedStep),
+                                  cudaMemcpyHostToDevice, c->stream),
+                  "cudaMemcpy(steps)");
+        QSIM_CUDA(cudaEventRecord(c->plan_ev, c->stream), "cudaEventRecord");
+        c->plan_ev_pending = true;
+    }
+    const int e = launch_row_array(d_rows, c->M, reinterpret_cast<const SlicedStep *>(c->d_plan),
+                                   (uint32_t)sl.size(), c->stream);
+    if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "row-array launch");
+    return QSIM_OK;
+}
+
 int qsim_read_state(qsim_ctx *c, void *host, size_t n_amps)
 {
     if (!c || !host) return fail(QSIM_EINVAL, "NULL argument");
@@ -342,6 +402,7 @@ int qsim_get_plan_stats(qsim_ctx *c, qsim_plan_stats *out)
 int qsim_synchronize(qsim_ctx *c)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    if (c->copy_stream) QSIM_CUDA(cudaStreamSynchronize(c->copy_stream), "probability copies");
     return check_device(c);
 }
 
@@ -487,25 +548,33 @@ int qsim_probabilities_device(qsim_ctx *c, double *d_probs, double *norm_out)
     return QSIM_OK;
 }
 
+namespace {
+
+// Queue the probabilities of the current state and their copy into host
+// memory (chunks double-buffered between the context's stream and its copy
+// stream); with norms, also the per-chunk norms.  Returns without waiting.
+int queue_host_probabilities(qsim_ctx *c, double *host_probs, bool norms, size_t *nchunks_out);
+
+}  // namespace
+
+int qsim_probabilities_async(qsim_ctx *c, double *host_probs, size_t n)
+{
+    if (!c || !host_probs) return fail(QSIM_EINVAL, "NULL argument");
+    if (n != c->n) return fail(QSIM_EINVAL, "n must equal 2^M");
+    size_t nchunks = 0;
+    return queue_host_probabilities(c, host_probs, false, &nchunks);
+}
+
 int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_out)
 {
     if (!c || !host_probs) return fail(QSIM_EINVAL, "NULL argument");
     if (n != c->n) return fail(QSIM_EINVAL, "n must equal 2^M");
     int rc = check_device(c);
     if (rc != QSIM_OK) return rc;
-    const size_t chunk = c->n < kProbChunk ? c->n : kProbChunk;
-    if (!c->d_probs_chunk) QSIM_CUDA(cudaMalloc(&c->d_probs_chunk, sizeof(double) * chunk), "cudaMalloc(probabilities)");
-    const size_t nchunks = (c->n + chunk - 1) / chunk;
-    const char *state = static_cast<const char *>(c->buf[c->cur]);
-    for (size_t k = 0; k < nchunks; ++k) {
-        int e = launch_probabilities(state + k * chunk * c->amp, (int)c->amp, chunk, c->d_probs_chunk,
-                                     c->d_partials, probabilities_partials_needed(),
-                                     norm_out ? c->d_norms + k : nullptr, c->stream);
-        if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
-        QSIM_CUDA(cudaMemcpyAsync(host_probs + k * chunk, c->d_probs_chunk, sizeof(double) * chunk,
-                                  cudaMemcpyDeviceToHost, c->stream),
-                  "cudaMemcpy(probabilities)");
-    }
+    size_t nchunks = 0;
+    rc = queue_host_probabilities(c, host_probs, norm_out != nullptr, &nchunks);
+    if (rc != QSIM_OK) return rc;
+    QSIM_CUDA(cudaStreamSynchronize(c->copy_stream), "cudaMemcpy(probabilities)");
     rc = check_device(c);
     if (rc != QSIM_OK) return rc;
     if (norm_out) {
@@ -523,6 +592,46 @@ int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_o
     }
     return QSIM_OK;
 }
+
+namespace {
+
+int queue_host_probabilities(qsim_ctx *c, double *host_probs, bool want_norms, size_t *nchunks_out)
+{
+    // Chunks of probabilities alternate between two device buffers: the kernel
+    // for chunk k+1 runs on the context's stream while chunk k is copied out
+    // on a second stream.
+    const size_t chunk = c->n < kProbChunk ? c->n : kProbChunk;
+    if (!c->copy_stream) {
+        QSIM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int i = 0; i < 2; ++i) {
+            QSIM_CUDA(cudaMalloc(&c->d_probs_chunk[i], sizeof(double) * chunk), "cudaMalloc(probabilities)");
+            QSIM_CUDA(cudaEventCreateWithFlags(&c->chunk_ready[i], cudaEventDisableTiming), "cudaEventCreate");
+            QSIM_CUDA(cudaEventCreateWithFlags(&c->chunk_copied[i], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    const size_t nchunks = (c->n + chunk - 1) / chunk;
+    *nchunks_out = nchunks;
+    const char *state = static_cast<const char *>(c->buf[c->cur]);
+    for (size_t k = 0; k < nchunks; ++k) {
+        const int b = (int)(k & 1);
+        // the buffer's previous chunk must be out before it is overwritten
+        // (also across calls: the events persist on the context)
+        QSIM_CUDA(cudaStreamWaitEvent(c->stream, c->chunk_copied[b], 0), "cudaStreamWaitEvent");
+        int e = launch_probabilities(state + k * chunk * c->amp, (int)c->amp, chunk, c->d_probs_chunk[b],
+                                     c->d_partials, probabilities_partials_needed(),
+                                     want_norms ? c->d_norms + k : nullptr, c->stream);
+        if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+        QSIM_CUDA(cudaEventRecord(c->chunk_ready[b], c->stream), "cudaEventRecord");
+        QSIM_CUDA(cudaStreamWaitEvent(c->copy_stream, c->chunk_ready[b], 0), "cudaStreamWaitEvent");
+        QSIM_CUDA(cudaMemcpyAsync(host_probs + k * chunk, c->d_probs_chunk[b], sizeof(double) * chunk,
+                                  cudaMemcpyDeviceToHost, c->copy_stream),
+                  "cudaMemcpy(probabilities)");
+        QSIM_CUDA(cudaEventRecord(c->chunk_copied[b], c->copy_stream), "cudaEventRecord");
+    }
+    return QSIM_OK;
+}
+
+}  // namespace
 
 int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, int strategy,
                       int tile_bits, int low_bits, int scratch_available, qsim_plan_stats *stats,

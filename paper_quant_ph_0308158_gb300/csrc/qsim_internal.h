@@ -85,6 +85,7 @@ struct TilePass {
     uint32_t step_off;  // offset of this pass's steps in the TileStep buffer
     uint32_t nsteps;
     uint32_t all_local; // 1 when no step has a control outside the tile
+    uint32_t affine;    // 1 when every step has at most one control (NOT/CNOT)
     double touched;     // estimated fraction of tiles with an active step
 };
 
@@ -179,6 +180,13 @@ int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d
                          double *d_partials, int n_partials, double *d_norm, void *stream);
 int probabilities_partials_needed();
 size_t batch_smem_bytes(uint32_t max_sliced_M);
+int launch_product_state(void *state, int amp_bytes, uint32_t M, const double *d_qubits, void *stream);
+int launch_row_array(uint64_t *d_rows, uint32_t M, const SlicedStep *d_steps, uint32_t nsteps,
+                     void *stream);
+// Bit-sliced descriptors of a step list (planner.cpp); QSIM_EINVAL for a step
+// with more controls than a descriptor holds.
+int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<SlicedStep> *out,
+                    std::string *msg);
 int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
                        uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream);
 size_t tile_smem_bytes(int amp_bytes, int k);

@@ -312,6 +312,23 @@ def config_adder(n: int = 13, seed: int = 3):
                 steps=steps, state_seed=seed, line_to_bit=l2b)
 
 
+def sec4_qubits(M: int) -> np.ndarray:
+    """The Sec. 4 input (1, -1, 1, -1, ...)/sqrt(2^M) as M qubits (App. 1):
+    (1, -1)/sqrt(2) on a(1) and (1, 1)/sqrt(2) on every other wire."""
+    s = 1.0 / math.sqrt(2.0)
+    q = np.empty((M, 2), dtype=np.complex128)
+    q[0] = (s, -s)
+    q[1:] = (s, s)
+    return q
+
+
+def config_parity(M: int = 32):
+    """Sec. 4 computational example: the parity of a(2)..a(M) onto a(1) on the
+    alternating input, generated on the device from its qubits (App. 1)."""
+    return dict(name="M%d_c64_parity_sec4" % M, M=M, dtype=np.complex64,
+                steps=parity_circuit(M), state_seed=None, qubits=sec4_qubits(M))
+
+
 def batch_specs(n: int = 4096, seed: int = 4, mix: str = "cnot",
                 m_range=(10, 22), l_range=(50, 2000)):
     """Independent circuits for the batched run: M ~ U{10..22},

@@ -291,3 +291,107 @@ def test_wide_indices_m33():
         sim.apply(both[::-1][150:].copy())         # tile / sweep passes, in place
         sim.synchronize()
         np.testing.assert_array_equal(sim.state_tensor()[ridx].cpu().numpy(), k1[rows.astype(np.int64)])
+
+
+# ----------------------------------------------------------------------------
+# App. 1: the input generated on the device from M qubits
+# ----------------------------------------------------------------------------
+
+# The device multiplies (high-bit partial product) x (low-bit partial product)
+# while the oracle multiplies the factors one by one from the top: at most
+# M complex products, each correctly rounded per real operation, so the two
+# differ by far less than 1e-13 of |k1(i)| in FP64.
+PRODUCT_RTOL = 1e-13
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("M", [1, 5, 10, 11, 16, 23])
+def test_product_state_input(dtype, M):
+    rng = np.random.default_rng(100 + M)
+    q = rng.normal(size=(M, 2)) + 1j * rng.normal(size=(M, 2))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    want = oracle.product_state(M, q)
+    with Simulator(M, dtype) as sim:
+        sim.load_product_state(q)
+        got = sim.read_state().astype(np.complex128)
+    if dtype == np.complex128:
+        assert np.all(np.abs(got - want) <= PRODUCT_RTOL * np.abs(want) + 1e-300)
+    else:  # rounded once to complex64 at the end: within one float ulp per part
+        w = want.astype(np.complex64).astype(np.complex128)
+        tol = np.spacing(np.abs(w.real).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(got.real - w.real) <= tol)
+        tol = np.spacing(np.abs(w.imag).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(got.imag - w.imag) <= tol)
+
+
+def test_product_state_exact_cases_and_sec4_input():
+    # integer components: every product is exact on both sides
+    M = 12
+    rng = np.random.default_rng(5)
+    q = rng.integers(-2, 3, size=(M, 2)) + 1j * rng.integers(-2, 3, size=(M, 2))
+    with Simulator(M, np.complex128) as sim:
+        sim.load_product_state(q)
+        np.testing.assert_array_equal(sim.read_state(), oracle.product_state(M, q))
+    # Sec. 4: (1, -1, 1, -1, ...)/sqrt(2^M) is the product of (1, -1)/sqrt2 on
+    # a(1) and (1, 1)/sqrt2 elsewhere (1/sqrt2 is itself rounded, so the
+    # product carries M rounding errors of the factor)
+    M = 16
+    q = W.sec4_qubits(M)
+    with Simulator(M, np.complex128) as sim:
+        sim.load_product_state(q)
+        got = sim.read_state()
+    np.testing.assert_allclose(got, W.alternating_state(M), rtol=PRODUCT_RTOL, atol=0)
+    np.testing.assert_allclose(got, oracle.product_state(M, q), rtol=PRODUCT_RTOL, atol=0)
+
+
+# ----------------------------------------------------------------------------
+# the row array of the product (Sec. 2h), kept as "information about the unitary"
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,L,seed", [(1, 3, 1), (3, 10, 2), (12, 500, 3), (20, 300, 4)])
+def test_row_array_equals_the_sec2h_product(M, L, seed):
+    import torch
+    steps = W.random_circuit(M, L, seed, max_controls=min(8, M - 1))
+    rows = torch.empty(1 << M, dtype=torch.int64, device="cuda")
+    with Simulator(M, np.complex64) as sim:
+        sim.row_array(steps, rows.data_ptr())
+        sim.synchronize()
+    np.testing.assert_array_equal(rows.cpu().numpy(), oracle.gather_map(M, steps))
+
+
+def test_row_array_rejects_steps_beyond_eight_controls():
+    import torch
+    M = 12
+    rows = torch.empty(1 << M, dtype=torch.int64, device="cuda")
+    with Simulator(M, np.complex64) as sim:
+        with pytest.raises(QsimError) as e:
+            sim.row_array(W.make_steps([(0, 0b1111111110, 0b1111111110)]), rows.data_ptr())
+        assert "more than 8 controls" in str(e.value)
+
+
+def test_async_load_and_probabilities_on_two_contexts():
+    """The copy-in / copy-out calls queued without waiting, alternating two
+    contexts on two streams as the end-to-end benchmark does."""
+    import torch
+    M = 18
+    steps = W.mixed_circuit(M, 300, 21)
+    states = [W.random_state(M, np.complex128, 21 + i) for i in range(4)]
+    want = [oracle.probabilities(oracle.apply_circuit(M, k, steps)) for k in states]
+    s2 = torch.cuda.Stream()
+    with Simulator(M, np.complex128) as a:
+        with torch.cuda.stream(s2):
+            b = Simulator(M, np.complex128)
+        sims = (a, b)
+        outs = [np.zeros(1 << M) for _ in range(4)]
+        for i in range(4):
+            sm = sims[i & 1]
+            if i >= 2:
+                sm.synchronize()
+            sm.load_state_async(states[i])
+            sm.apply(steps)
+            sm.probabilities_async(outs[i])
+        for sm in sims:
+            sm.synchronize()
+        b.close()
+    for i in range(4):
+        assert_probs_close(outs[i], want[i])

@@ -40,6 +40,10 @@ MUTANTS = {
     "gather_transposed": ("for (int64_t i = 0; i < n; ++i) k2[i] = k1[x[i]];",
                           "for (int64_t i = 0; i < n; ++i) k2[x[i]] = k1[i];"),
     "probability_term_dropped": ("p[i] = a + b;", "p[i] = a;"),
+    "product_bits_reversed": ("const ocplx f = q[2 * b + ((i >> b) & 1u)];",
+                              "const ocplx f = q[2 * b + ((i >> (M - 1 - b)) & 1u)];"),
+    "product_conjugate_term": ("const double im = acc.re * f.im + acc.im * f.re;",
+                               "const double im = acc.re * f.im - acc.im * f.re;"),
     "control_test_inverted": ("if (!toggled(st, i)) continue;\n            ocplx tmp",
                               "if (toggled(st, i)) continue;\n            ocplx tmp"),
 }
@@ -58,6 +62,8 @@ PINS = [
     (pins.test_cnot_circuits_equal_their_gf2_affine_map, {}),
     (pins.test_adder_small_full_state, {}),
     (pins.test_probabilities_pins, {}),
+    (pins.test_app1_product_state_example_and_kron, {}),
+    (pins.test_app1_product_state_norm_and_random_qubits, {}),
 ]
 
 
@@ -80,7 +86,7 @@ def test_mutant_is_caught(name, tmp_path, monkeypatch):
     lib = ctypes.CDLL(so)
     for fn in ("oracle_validate", "oracle_step_row_array", "oracle_paper_product",
                "oracle_gather_map", "oracle_gather", "oracle_apply_circuit",
-               "oracle_source_rows", "oracle_probabilities", "oracle_sum"):
+               "oracle_source_rows", "oracle_product_state", "oracle_probabilities", "oracle_sum"):
         f, g = getattr(lib, fn), getattr(real, fn)
         f.argtypes, f.restype = g.argtypes, g.restype
     monkeypatch.setattr(oracle, "_lib", lib)

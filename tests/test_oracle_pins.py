@@ -323,3 +323,38 @@ def test_validation_rejects_invalid_steps():
     assert not oracle.validate(M, W.make_steps([(0, 16, 16)]))      # control wire absent
     with pytest.raises(ValueError):
         oracle.apply_circuit(M, np.zeros(16, np.complex128), W.make_steps([(4, 0, 0)]))
+
+
+# ----------------------------------------------------------------------------
+# App. 1: product-state input
+# ----------------------------------------------------------------------------
+
+def test_app1_product_state_example_and_kron():
+    """k1 = q_M (x) ... (x) q_1; e.g. k1(5) = q3(1) q2(0) q1(1) (App. 1)."""
+    M = 3
+    # distinct primes make every product identify its factors; integers keep it exact
+    q = np.array([[2, 3], [5, 7], [11, 13]], dtype=np.complex128)  # q1, q2, q3
+    k = oracle.product_state(M, q)
+    assert k[5] == q[2][1] * q[1][0] * q[0][1] == 13 * 5 * 3
+    ref = np.kron(q[2], np.kron(q[1], q[0]))  # library Kronecker product
+    np.testing.assert_array_equal(k, ref)
+    # complex integer components stay exact as well
+    rng = np.random.default_rng(0)
+    qi = rng.integers(-4, 5, size=(6, 2)) + 1j * rng.integers(-4, 5, size=(6, 2))
+    ref = qi[5]
+    for b in range(4, -1, -1):
+        ref = np.kron(ref, qi[b])
+    np.testing.assert_array_equal(oracle.product_state(6, qi), ref)
+
+
+def test_app1_product_state_norm_and_random_qubits():
+    M = 12
+    rng = np.random.default_rng(1)
+    q = rng.normal(size=(M, 2)) + 1j * rng.normal(size=(M, 2))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    k = oracle.product_state(M, q)
+    ref = q[M - 1]
+    for b in range(M - 2, -1, -1):
+        ref = np.kron(ref, q[b])
+    np.testing.assert_allclose(k, ref, rtol=1e-14, atol=1e-17)
+    assert abs(oracle.fsum_pairwise(oracle.probabilities(k)) - 1.0) < 1e-13
