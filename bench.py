@@ -4,9 +4,12 @@
                     [--workload mixed_m28|adder_m32|cnot_m16]
 
 One timed step = one pass of the whole hot path over the resident state:
-validate + plan the circuit, apply all of its steps (qsim_apply_circuit) and
-compute the FP64 basis-state probabilities into device memory
-(qsim_probabilities_device).  value = 2^M * L * K / (device time of K steps).
+validate + plan the circuit, apply all of its steps and compute the FP64
+basis-state probabilities into device memory, through
+qsim_apply_circuit_probabilities (the last pass writes the probabilities
+beside the state; --separate-probs times qsim_apply_circuit followed by
+qsim_probabilities_device instead).  value = 2^M * L * K / (device time of
+K steps).
 
 Default workload: M=28 complex128 (4 GiB state, larger than L2), L=1000 steps
 of the NOT / CNOT / Toffoli / 3-5-control NOT mix, seeded synthetic state and
@@ -299,8 +302,11 @@ def run_ours(args, rank, ws, local):
     stream = torch.cuda.current_stream()
 
     def step():
-        sim.apply(steps)
-        sim.probabilities_device(probs.data_ptr())
+        if args.separate_probs:
+            sim.apply(steps)
+            sim.probabilities_device(probs.data_ptr())
+        else:
+            sim.apply_probabilities(steps, probs.data_ptr())
 
     # ---- device-resident timing ------------------------------------------------
     load_input()
@@ -447,6 +453,8 @@ def run_ours(args, rank, ws, local):
                        "steps_cancelled": stats["steps_cancelled"],
                        "full_pass_equiv": stats["full_pass_equiv"],
                        "step_includes": "plan + all passes + FP64 probabilities",
+                       "probabilities": "separate pass" if args.separate_probs
+                       else "written by the last pass",
                        "jit": bool(jit_ms is not None),
                        "jit_compile_ms": jit_ms,
                        "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in by_kind.items()}},
@@ -573,6 +581,39 @@ def run_batch(args, rank, ws, local):
     return 0
 
 
+def serve_plain_baseline(specs, pool):
+    """The same requests one at a time through the plain API, back to back:
+    load the state from pinned host memory, apply the circuit, copy the FP64
+    probabilities to pinned host memory, then the next request (one context
+    per M, created before timing)."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Simulator
+
+    sims, outs = {}, {}
+    for M in sorted({sp["M"] for sp in specs}):
+        sims[M] = Simulator(M, np.complex128)
+        outs[M] = torch.empty(1 << M, dtype=torch.float64, pin_memory=True).numpy()
+    for sp in specs[:3]:  # warm-up
+        sims[sp["M"]].load_state(pool[sp["M"]][1])
+        sims[sp["M"]].apply(sp["steps"])
+        sims[sp["M"]].probabilities(out=outs[sp["M"]])
+    torch.cuda.synchronize()
+    amp_steps = 0.0
+    t0 = time.perf_counter()
+    for sp in specs:
+        sim = sims[sp["M"]]
+        sim.load_state(pool[sp["M"]][1])
+        sim.apply(sp["steps"])
+        sim.probabilities(out=outs[sp["M"]])
+        amp_steps += float(1 << sp["M"]) * sp["L"]
+    wall = time.perf_counter() - t0
+    for sim in sims.values():
+        sim.close()
+    return {"requests": len(specs), "wall_s": wall, "value": amp_steps / wall,
+            "requests_per_s": len(specs) / wall,
+            "how": "first requests of the same stream, one at a time, closed loop"}
+
+
 def run_serve(args, rank, ws, local):
     """Serving: a Poisson stream of simulation requests through qsim_server
     (continuous batching under an HBM budget), FP64 probabilities out.
@@ -627,6 +668,8 @@ def run_serve(args, rank, ws, local):
     srv.close()
     lat_a = np.array(lat)
     value = amp_steps / wall
+    plain = serve_plain_baseline(specs[:args.serve_plain_requests], pool) \
+        if args.serve_plain_requests > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(specs),
         "warmup": 0, "ms_per_step": 1e3 * wall / len(specs), "higher_is_better": True,
@@ -640,7 +683,9 @@ def run_serve(args, rank, ws, local):
                    "latency_ms_p99": float(np.percentile(lat_a, 99)),
                    "latency_ms_max": float(lat_a.max()), "wall_s": wall,
                    "rounds": st["rounds"], "peak_hbm_in_use": st["peak_in_use_bytes"],
-                   "step": "one request (submit to FP64 probabilities in host memory)"},
+                   "step": "one request (submit to FP64 probabilities in host memory)",
+                   "plain": plain,
+                   "served_over_plain": value / plain["value"] if plain else None},
         "roofline": None, "cpu_baseline": None, "e2e": {"value": value, "unit": UNIT,
                    "h2d_bytes_per_step": float(np.mean([16 << sp["M"] for sp in specs])),
                    "d2h_bytes_per_step": float(np.mean([8 << sp["M"] for sp in specs]))},
@@ -661,11 +706,15 @@ def main():
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
     ap.add_argument("--low-bits", type=int, default=0, help="contiguous low tile bits l (0: default)")
+    ap.add_argument("--separate-probs", action="store_true",
+                    help="compute probabilities in their own pass after the circuit")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-m-max", type=int, default=30)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-host-gb", type=float, default=48.0)
+    ap.add_argument("--serve-plain-requests", type=int, default=400,
+                    help="requests timed one at a time for the plain comparison (0: skip)")
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
     ap.add_argument("--ref-steps-per-step", type=int, default=2,
                     help="oracle steps per timed reference step")

@@ -154,6 +154,18 @@ void *qsim_state_device(qsim_ctx *ctx);
  * next qsim_synchronize / qsim_read_state / qsim_probabilities. */
 int qsim_apply_circuit(qsim_ctx *ctx, const qsim_step *steps, size_t L);
 
+/* qsim_apply_circuit followed by the FP64 probabilities of the new state
+ * (the post-processing of Sec. 2b) into device memory d_probs (2^M doubles,
+ * 8-byte aligned; not NULL), with the same results as qsim_apply_circuit +
+ * qsim_probabilities_device(ctx, d_probs, NULL).  When the plan's last pass
+ * is a tile or gather pass, that pass writes the probabilities beside the
+ * amplitudes it stores (a tile pass then visits every tile), saving one
+ * read of the state; otherwise a separate pass computes them.  Queued on
+ * the context's stream like qsim_apply_circuit.  QSIM_EINVAL for a NULL or
+ * misaligned d_probs or an invalid circuit (nothing is queued then). */
+int qsim_apply_circuit_probabilities(qsim_ctx *ctx, const qsim_step *steps, size_t L,
+                                     double *d_probs);
+
 /* The row array of the circuit's product (Sec. 2h) -- the information about
  * the unitary matrix that the paper's conclusions propose to keep for design
  * automation: d_rows[i] = x(i) with k2(i) = k1(x(i)) for k2 = U_L ... U_1 k1,
@@ -213,9 +225,11 @@ int qsim_synchronize(qsim_ctx *ctx);
 
 /* ---- post-processing ----------------------------------------------------- */
 
-/* FP64 basis-state probabilities p(i) = re^2 + im^2 (products rounded
- * separately, no fused multiply-add) into host_probs[0 .. 2^M-1]; n must be
- * 2^M.  norm_out (may be NULL) receives sum_i p(i), reduced in FP64 on the
+/* FP64 basis-state probabilities p(i) = re^2 + im^2 into
+ * host_probs[0 .. 2^M-1]; n must be 2^M.  complex64: the squares are exact
+ * in FP64 and the sum is rounded once (identical to separately rounded
+ * products).  complex128: im^2 rounded, then one fused multiply-add (within
+ * one unit in the last place of separately rounded products).  norm_out (may be NULL) receives sum_i p(i), reduced in FP64 on the
  * device.  Synchronous. */
 int qsim_probabilities(qsim_ctx *ctx, double *host_probs, size_t n, double *norm_out);
 

@@ -41,7 +41,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 # every symbol include/qsim.h declares
 EXPORTS = (
     "qsim_create", "qsim_create_with_buffers", "qsim_destroy", "qsim_load_state",
-    "qsim_read_state", "qsim_state_device", "qsim_apply_circuit", "qsim_set_strategy",
+    "qsim_read_state", "qsim_state_device", "qsim_apply_circuit",
+    "qsim_apply_circuit_probabilities", "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
@@ -121,6 +122,7 @@ def load() -> ctypes.CDLL:
             "qsim_read_state": ([p, p, sz], i),
             "qsim_state_device": ([p], p),
             "qsim_apply_circuit": ([p, p, sz], i),
+            "qsim_apply_circuit_probabilities": ([p, p, sz, p], i),
             "qsim_set_strategy": ([p, i, i, i], i),
             "qsim_set_canonicalize": ([p, i], i),
             "qsim_set_profiling": ([p, i], i),
@@ -325,6 +327,13 @@ class Simulator:
     def apply(self, steps):
         s = as_steps(steps)
         _check(self._lib.qsim_apply_circuit(self._ctx, _ptr(s), len(s)))
+
+    def apply_probabilities(self, steps, out_ptr: int):
+        """apply(steps), then FP64 probabilities into device memory at out_ptr
+        (2^M doubles), written by the last pass where its kernel can."""
+        s = as_steps(steps)
+        _check(self._lib.qsim_apply_circuit_probabilities(self._ctx, _ptr(s), len(s),
+                                                          ctypes.c_void_p(out_ptr)))
 
     def set_profiling(self, enable: bool):
         _check(self._lib.qsim_set_profiling(self._ctx, int(bool(enable))))

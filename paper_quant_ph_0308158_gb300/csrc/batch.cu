@@ -337,7 +337,8 @@ int qsim_batch_run_plain(qsim_batch *b)
             if (ps.kind == kSweep) {
                 e = launch_sweep(a_in, (int)b->amp, ps.sweep, nullptr, b->stream);
             } else {
-                e = launch_gather(a_in, a_out, (int)b->amp, b->M[i], ps.gather, tab, sl, nullptr, b->stream);
+                e = launch_gather(a_in, a_out, (int)b->amp, b->M[i], ps.gather, tab, sl, nullptr, nullptr,
+                                  b->stream);
                 cur = 1 - cur;
             }
             if (e != cudaSuccess)

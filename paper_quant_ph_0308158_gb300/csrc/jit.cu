@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "prob_math.cuh"
 #include "qsim_internal.h"
 
 namespace qsim {
@@ -140,8 +141,11 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
          "    for (int k = 0; k < 32; ++k) { if (k & j) continue;\n"
          "      const u32 t = ((a[k] >> j) ^ a[k | j]) & m; a[k | j] ^= t; a[k] ^= t << j; }\n"
          "  }\n}\n";
+    // FP64 probabilities of the gathered amplitudes (same functions as the
+    // library's own kernels)
+    s << "#define QSIM_Q __device__ __forceinline__\n" << kProbMathSource << "\n";
     s << "extern \"C\" __global__ void __launch_bounds__(256) qsim_jit_gather("
-         "const Amp* __restrict__ in, Amp* __restrict__ out, u64 n) {\n"
+         "const Amp* __restrict__ in, Amp* __restrict__ out, u64 n, double* __restrict__ probs) {\n"
          "  __shared__ u32 tabs[8 * 32 * 33];\n";
     if (wide) s << "  __shared__ unsigned char his[8 * 32 * 33];\n";
     s << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
@@ -198,10 +202,17 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
          "        o[u] = wbase + (u64)(e0 + u) * 32ull + lane;\n"
          "        u64 x = tab[(e0 + u) * 33 + lane];\n";
     if (wide) s << "        x |= (u64)hi[(e0 + u) * 33 + lane] << 32;\n";
+    // probabilities beside the stores (a uniform test: one kernel serves both)
     s << "        if (o[u] < n) v[u] = ldnc(in + x);\n"
          "      }\n"
          "#pragma unroll\n"
-         "      for (int u = 0; u < 8; ++u) if (o[u] < n) out[o[u]] = v[u];\n"
+         "      for (int u = 0; u < 8; ++u) if (o[u] < n) {\n"
+         "        out[o[u]] = v[u];\n"
+         "        if (probs) probs[o[u]] = "
+      << (amp == 16 ? "qsim_prob_bits(v[u].a, v[u].b, v[u].c, v[u].d)"
+                    : "qsim_prob_bits(v[u].a, v[u].b)")
+      << ";\n"
+         "      }\n"
          "    }\n"
          "    __syncwarp();\n"
          "  }\n}\n";
@@ -282,7 +293,7 @@ int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *c
 }
 
 int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
-                      size_t n, void *stream, std::string *msg)
+                      size_t n, double *d_probs, void *stream, std::string *msg)
 {
     JitEntry *e = nullptr;
     int rc = jit_get(M, amp, steps, n, true, &e, msg);
@@ -294,7 +305,8 @@ int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim
     const void *a0 = in;
     void *a1 = out;
     uint64_t a2 = total;
-    void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2};
+    double *a3 = d_probs;
+    void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2, (void *)&a3};
     cudaError_t ce = cudaLaunchKernel(reinterpret_cast<const void *>(e->kern), dim3(grid), dim3(256),
                                       args, 0, static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) {

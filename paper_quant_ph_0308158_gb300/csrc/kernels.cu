@@ -24,6 +24,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "prob_math.cuh"
 #include "qsim_internal.h"
 
 namespace qsim {
@@ -36,6 +37,11 @@ constexpr unsigned kWaitLimit = 1u << 24;  // bounded mbarrier polls (seconds)
 template <int B> struct AmpOf;
 template <> struct AmpOf<8> { using T = uint2; };
 template <> struct AmpOf<16> { using T = uint4; };
+
+// FP64 probability of one amplitude held as raw words (prob_math.cuh)
+QSIM_PROB_MATH(__device__ __forceinline__)
+__device__ __forceinline__ double amp_prob(const uint2 &v) { return qsim_prob_bits(v.x, v.y); }
+__device__ __forceinline__ double amp_prob(const uint4 &v) { return qsim_prob_bits(v.x, v.y, v.z, v.w); }
 
 // Insert a zero bit at position pos of x (bits >= pos move up by one).
 __device__ __forceinline__ uint64_t insert_zero(uint64_t x, uint32_t pos)
@@ -150,6 +156,7 @@ constexpr int kMaskWords = kMaxTileSteps / 32;
 
 struct TileKParams {
     char *state;
+    double *probs;                 // non-null: also write FP64 probabilities (every tile)
     const TileStep *steps;
     int *err;
     uint64_t n_tiles;
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                     mask[w] = __ballot_sync(0xffffffffu, act);
                     any |= mask[w] != 0;
                 }
-                if (any) break;
+                if (any || p.probs) break;  // a pass that writes probabilities visits every tile
                 base = kNoTile;
             }
             bool same = have_last && base != kNoTile;
@@ -333,6 +340,17 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
         }
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
+        bool idle = true;  // no active step: only a pass writing probabilities sends such a tile
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) idle = idle && meta[s].mask[w] == 0u;
+        if (idle) {
+            const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
+            for (uint32_t j = tid; j < tile_amps; j += kTileThreads)
+                p.probs[base + depo[j >> p.l] + (j & lmask)] = amp_prob(buf[j]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            continue;
+        }
         if (!meta[s].same && p.affine && have_perm) {
             // NOT/CNOT segment: every tile's map is A j ^ c(tile) with the same
             // A, so the table of the first tile is reused with c(tile) ^ c(first)
@@ -382,7 +400,11 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const uint32_t j = j0 + tid + e * kTileThreads;
-                if (j < tile_amps) st[base + depo[j >> p.l] + (j & lmask)] = v[e];
+                if (j < tile_amps) {
+                    const uint64_t g = base + depo[j >> p.l] + (j & lmask);
+                    st[g] = v[e];
+                    if (p.probs) p.probs[g] = amp_prob(v[e]);
+                }
             }
         }
         __syncwarp();
@@ -399,7 +421,8 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 template <int B, bool WIDE, typename I>
 __device__ __forceinline__ void affine_range(const char *__restrict__ in, char *__restrict__ out,
                                              uint64_t o0, uint64_t o1, uint64_t step,
-                                             const I *tab, uint32_t nbytes, uint64_t bvec)
+                                             const I *tab, uint32_t nbytes, uint64_t bvec,
+                                             double *__restrict__ probs)
 {
     using A = typename AmpOf<B>::T;
     const A *src = reinterpret_cast<const A *>(in);
@@ -419,7 +442,10 @@ __device__ __forceinline__ void affine_range(const char *__restrict__ in, char *
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (idx[u] < o1) dst[idx[u]] = v[u];
+            if (idx[u] < o1) {
+                dst[idx[u]] = v[u];
+                if (probs) probs[idx[u]] = amp_prob(v[u]);
+            }
     }
 }
 
@@ -427,14 +453,15 @@ template <int B, bool WIDE>
 __global__ void __launch_bounds__(kThreads) gather_affine_kernel(const char *__restrict__ in,
                                                                  char *__restrict__ out, uint64_t n,
                                                                  const uint64_t *__restrict__ tables,
-                                                                 uint32_t nbytes, uint64_t bvec)
+                                                                 uint32_t nbytes, uint64_t bvec,
+                                                                 double *__restrict__ probs)
 {
     using I = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
     __shared__ I tab[5 * 256];
     for (uint32_t i = threadIdx.x; i < nbytes * 256; i += kThreads) tab[i] = (I)tables[i];
     __syncthreads();
     affine_range<B, WIDE, I>(in, out, (uint64_t)blockIdx.x * kThreads + threadIdx.x, n,
-                             (uint64_t)gridDim.x * kThreads, tab, nbytes, bvec);
+                             (uint64_t)gridDim.x * kThreads, tab, nbytes, bvec, probs);
 }
 
 // Bit-sliced gather.  Each thread owns 64 consecutive output indices
@@ -494,7 +521,7 @@ __host__ __device__ constexpr size_t sliced_smem_for(uint32_t M)
 template <int B, bool WIDE, bool MAP = false>
 __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out, uint32_t M,
                              uint64_t n, const SlicedStep *__restrict__ steps, uint32_t nsteps,
-                             uint64_t cbase, unsigned char *smem)
+                             uint64_t cbase, unsigned char *smem, double *__restrict__ probs)
 {
     using A = typename AmpOf<B>::T;
     // planes: [M + 1][kThreads] u64 ; table: [8 warps][32][33] u32 ;
@@ -591,7 +618,10 @@ __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out
             if (!MAP) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (o[u] < n) dst[o[u]] = v[u];
+                    if (o[u] < n) {
+                        dst[o[u]] = v[u];
+                        if (probs) probs[o[u]] = amp_prob(v[u]);
+                    }
             }
         }
     }
@@ -601,13 +631,13 @@ __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out
 template <int B, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 2) gather_sliced_kernel(
     const char *__restrict__ in, char *__restrict__ out, uint32_t M, uint64_t n,
-    const SlicedStep *__restrict__ steps, uint32_t nsteps)
+    const SlicedStep *__restrict__ steps, uint32_t nsteps, double *__restrict__ probs)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint64_t per_iter = (uint64_t)gridDim.x * kSlicedOutputs;
     // the loop bound is uniform over the CTA, so the barriers inside are safe
     for (uint64_t cbase = (uint64_t)blockIdx.x * kSlicedOutputs; cbase < n; cbase += per_iter)
-        sliced_chunk<B, WIDE>(in, out, M, n, steps, nsteps, cbase, smem);
+        sliced_chunk<B, WIDE>(in, out, M, n, steps, nsteps, cbase, smem, probs);
 }
 
 // Row array of the product of a step list: rows[i] = x(i) for every output
@@ -622,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 2) row_array_kernel(uint64_t *__rest
     const uint64_t per_iter = (uint64_t)gridDim.x * kSlicedOutputs;
     for (uint64_t cbase = (uint64_t)blockIdx.x * kSlicedOutputs; cbase < n; cbase += per_iter)
         sliced_chunk<8, WIDE, true>(nullptr, reinterpret_cast<char *>(rows), M, n, steps, nsteps,
-                                    cbase, smem);
+                                    cbase, smem, nullptr);
 }
 
 // Sweep of pair indices [q0, q1) of one step (in place).
@@ -678,10 +708,10 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__rest
                 if (threadIdx.x == 0) s_tables = (int32_t)item.pass;
             }
             affine_range<B, WIDE, I>(P.in, P.out, item.start + threadIdx.x, o1, kThreads, tab,
-                                     P.nbytes, P.bvec);
+                                     P.nbytes, P.bvec, nullptr);
         } else if (P.kind == 4) {
             if (threadIdx.x == 0) s_tables = -1;
-            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem);
+            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem, nullptr);
         } else {
             sweep_range<B>(P.out, P.sweep, item.start + threadIdx.x, o1, kThreads);
         }
@@ -753,20 +783,8 @@ constexpr int kProbBlocks = 1024;
 template <int B>
 __device__ __forceinline__ double prob_of(const char *__restrict__ state, uint64_t i)
 {
-    double re, im;
-    if (B == 8) {
-        const float2 v = __ldcs(reinterpret_cast<const float2 *>(state) + i);
-        re = (double)v.x;
-        im = (double)v.y;
-    } else {
-        const double2 v = __ldcs(reinterpret_cast<const double2 *>(state) + i);
-        re = v.x;
-        im = v.y;
-    }
-    // re^2 + im^2 with im^2 rounded and one fused multiply-add: within one
-    // unit in the last place of the separately rounded sum, one FP64
-    // instruction fewer (FP64 issue rate bounds this kernel on GB300)
-    return __fma_rn(re, re, __dmul_rn(im, im));
+    using A = typename AmpOf<B>::T;
+    return amp_prob(__ldcs(reinterpret_cast<const A *>(state) + i));
 }
 
 template <int B, bool NORM>
@@ -881,10 +899,11 @@ size_t tile_smem_bytes(int amp_bytes, int k)
 }
 
 int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d_steps,
-                int *d_err, void *stream)
+                int *d_err, double *d_probs, void *stream)
 {
     TileKParams p;
     p.state = static_cast<char *>(state);
+    p.probs = d_probs;
     p.steps = d_steps + t.step_off;
     p.err = d_err;
     p.n_tiles = t.n_tiles;
@@ -947,7 +966,8 @@ static size_t sliced_smem_bytes(uint32_t M) { return sliced_smem_for(M); }
 
 template <int B, bool W>
 static cudaError_t launch_sliced(const void *in, void *out, uint32_t M, uint64_t n,
-                                 const SlicedStep *steps, uint32_t nsteps, cudaStream_t s)
+                                 const SlicedStep *steps, uint32_t nsteps, double *probs,
+                                 cudaStream_t s)
 {
     const size_t smem = sliced_smem_bytes(M);
     cudaError_t e = cudaFuncSetAttribute(gather_sliced_kernel<B, W>,
@@ -961,13 +981,13 @@ static cudaError_t launch_sliced(const void *in, void *out, uint32_t M, uint64_t
     const uint64_t cap = (uint64_t)num_sms() * per_sm;
     const int grid = (int)(chunks < cap ? chunks : cap);
     gather_sliced_kernel<B, W><<<grid, kThreads, smem, s>>>(
-        static_cast<const char *>(in), static_cast<char *>(out), M, n, steps, nsteps);
+        static_cast<const char *>(in), static_cast<char *>(out), M, n, steps, nsteps, probs);
     return cudaGetLastError();
 }
 
 int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &g,
                   const uint64_t *d_tables, const SlicedStep *d_steps, int * /*d_err*/,
-                  void *stream)
+                  double *d_probs, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t n = 1ull << M;
@@ -980,23 +1000,23 @@ int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const Ga
         char *o = static_cast<char *>(out);
         if (amp_bytes == 8) {
             if (M > 32)
-                gather_affine_kernel<8, true><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec);
+                gather_affine_kernel<8, true><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec, d_probs);
             else
-                gather_affine_kernel<8, false><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec);
+                gather_affine_kernel<8, false><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec, d_probs);
         } else {
             if (M > 32)
-                gather_affine_kernel<16, true><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec);
+                gather_affine_kernel<16, true><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec, d_probs);
             else
-                gather_affine_kernel<16, false><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec);
+                gather_affine_kernel<16, false><<<grid, kThreads, 0, s>>>(i, o, n, tab, g.nbytes, g.bvec, d_probs);
         }
         return cudaGetLastError();
     }
     const SlicedStep *st = d_steps + g.step_off;
     if (amp_bytes == 8)
-        return M > 32 ? launch_sliced<8, true>(in, out, M, n, st, g.nsteps, s)
-                      : launch_sliced<8, false>(in, out, M, n, st, g.nsteps, s);
-    return M > 32 ? launch_sliced<16, true>(in, out, M, n, st, g.nsteps, s)
-                  : launch_sliced<16, false>(in, out, M, n, st, g.nsteps, s);
+        return M > 32 ? launch_sliced<8, true>(in, out, M, n, st, g.nsteps, d_probs, s)
+                      : launch_sliced<8, false>(in, out, M, n, st, g.nsteps, d_probs, s);
+    return M > 32 ? launch_sliced<16, true>(in, out, M, n, st, g.nsteps, d_probs, s)
+                  : launch_sliced<16, false>(in, out, M, n, st, g.nsteps, d_probs, s);
 }
 
 int probabilities_partials_needed() { return kProbBlocks; }

@@ -406,9 +406,48 @@ int qsim_synchronize(qsim_ctx *c)
     return check_device(c);
 }
 
-int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
+// Record the start of a profiled launch of kernel kind 'kind' with the given
+// algorithmic bytes; returns the event slot (or -1 without profiling).
+static int prof_begin(qsim_ctx *c, uint32_t kind, double bytes)
+{
+    if (!c->profiling) return -1;
+    const size_t slot = c->prof_kinds.size();
+    while (c->ev.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -2;
+        c->ev.push_back(e);
+    }
+    if (cudaEventRecord(c->ev[2 * slot], c->stream) != cudaSuccess) return -2;
+    c->prof_kinds.push_back(kind);
+    c->prof_bytes.push_back(bytes);
+    return (int)slot;
+}
+
+static int prof_end(qsim_ctx *c, int slot)
+{
+    if (slot == -2) return fail(QSIM_ECUDA, "profiling events");
+    if (slot < 0) return QSIM_OK;
+    QSIM_CUDA(cudaEventRecord(c->ev[2 * (size_t)slot + 1], c->stream), "cudaEventRecord");
+    return QSIM_OK;
+}
+
+// FP64 probabilities of the current state into device memory (no norm).
+static int probabilities_pass(qsim_ctx *c, double *d_probs)
+{
+    const int slot = prof_begin(c, 6, (double)c->n * (double)(c->amp + 8));
+    const int e = launch_probabilities(c->buf[c->cur], (int)c->amp, c->n, d_probs, c->d_partials,
+                                       probabilities_partials_needed(), nullptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+    return prof_end(c, slot);
+}
+
+// Apply a circuit; with d_probs also write the FP64 probabilities of the
+// result, from the last pass when its kernel can (tile and gather passes),
+// else by a probabilities pass after it.
+static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_probs)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    if (reinterpret_cast<uintptr_t>(d_probs) & 7u) return fail(QSIM_EINVAL, "d_probs misaligned");
     Plan plan;
     std::string msg;
     PlanOptions o = c->opts;
@@ -416,7 +455,7 @@ int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
     int rc = make_plan(c->M, steps, L, o, &plan, &msg);
     if (rc != QSIM_OK) return fail(rc, msg);
     fill_stats(plan, c->M, c->amp, &c->stats);
-    if (plan.passes.empty()) return QSIM_OK;
+    if (plan.passes.empty()) return d_probs ? probabilities_pass(c, d_probs) : QSIM_OK;
 
     bool need_scratch = false;
     for (const Pass &p : plan.passes) need_scratch |= (p.kind == kGather);
@@ -443,46 +482,56 @@ int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
         QSIM_CUDA(cudaEventRecord(c->plan_ev, c->stream), "cudaEventRecord");
         c->plan_ev_pending = true;
     }
-    const size_t prof0 = c->prof_kinds.size();  // passes recorded since the last read
-    if (c->profiling) {
-        while (c->ev.size() < 2 * (prof0 + plan.passes.size())) {
-            cudaEvent_t e;
-            QSIM_CUDA(cudaEventCreate(&e), "cudaEventCreate(profiling)");
-            c->ev.push_back(e);
-        }
-    }
     const TileStep *d_tile = reinterpret_cast<const TileStep *>(c->d_plan + off_tile);
     const SlicedStep *d_sliced = reinterpret_cast<const SlicedStep *>(c->d_plan + off_sliced);
     const uint64_t *d_tab = reinterpret_cast<const uint64_t *>(c->d_plan + off_tab);
+    const double n = (double)c->n;
+    bool fused = false;
     for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
         const Pass &p = plan.passes[pi];
-        int e = cudaSuccess;
-        if (c->profiling) {
-            QSIM_CUDA(cudaEventRecord(c->ev[2 * (prof0 + pi)], c->stream), "cudaEventRecord");
-            c->prof_kinds.push_back(pass_variant(p));
-            c->prof_bytes.push_back(p.alg_bytes);
+        // the last pass writes the probabilities when its kernel can
+        double *pp = (d_probs && pi + 1 == plan.passes.size() && p.kind != kSweep) ? d_probs : nullptr;
+        double bytes = p.alg_bytes;
+        if (pp) {
+            // every tile is read; touched tiles are written; plus the probabilities
+            bytes = (p.kind == kTile ? n * c->amp + 0.5 * p.alg_bytes : p.alg_bytes) + 8.0 * n;
+            fused = true;
         }
+        const int slot = prof_begin(c, pass_variant(p), bytes);
+        int e = cudaSuccess;
         if (p.kind == kSweep) {
             e = launch_sweep(c->buf[c->cur], (int)c->amp, p.sweep, c->d_err, c->stream);
         } else if (p.kind == kTile) {
-            e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, c->stream);
+            e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, pp, c->stream);
         } else if (p.gather.jit) {
             std::string jmsg;
             const int jrc = launch_jit_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M,
                                               plan.jit_steps.data() + p.gather.jit_off,
-                                              p.gather.jit_n, c->stream, &jmsg);
+                                              p.gather.jit_n, pp, c->stream, &jmsg);
             if (jrc != QSIM_OK) return fail(jrc, jmsg);
             c->cur = 1 - c->cur;
         } else {
             e = launch_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M, p.gather,
-                              d_tab, d_sliced, c->d_err, c->stream);
+                              d_tab, d_sliced, c->d_err, pp, c->stream);
             if (e == cudaSuccess) c->cur = 1 - c->cur;
         }
         if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "kernel launch");
-        if (c->profiling)
-            QSIM_CUDA(cudaEventRecord(c->ev[2 * (prof0 + pi) + 1], c->stream), "cudaEventRecord");
+        const int prc = prof_end(c, slot);
+        if (prc != QSIM_OK) return prc;
     }
+    if (d_probs && !fused) return probabilities_pass(c, d_probs);
     return QSIM_OK;
+}
+
+int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
+{
+    return apply_impl(c, steps, L, nullptr);
+}
+
+int qsim_apply_circuit_probabilities(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_probs)
+{
+    if (!d_probs) return fail(QSIM_EINVAL, "d_probs is NULL");
+    return apply_impl(c, steps, L, d_probs);
 }
 
 int qsim_set_profiling(qsim_ctx *c, int enable)
@@ -522,24 +571,13 @@ int qsim_probabilities_device(qsim_ctx *c, double *d_probs, double *norm_out)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
     if (reinterpret_cast<uintptr_t>(d_probs) & 7u) return fail(QSIM_EINVAL, "d_probs misaligned");
-    const size_t prof0 = c->prof_kinds.size();
-    if (c->profiling) {
-        while (c->ev.size() < 2 * (prof0 + 1)) {
-            cudaEvent_t ev;
-            QSIM_CUDA(cudaEventCreate(&ev), "cudaEventCreate(profiling)");
-            c->ev.push_back(ev);
-        }
-        QSIM_CUDA(cudaEventRecord(c->ev[2 * prof0], c->stream), "cudaEventRecord");
-    }
+    const int slot = prof_begin(c, 6, (double)c->n * (double)(c->amp + (d_probs ? 8 : 0)));
     int e = launch_probabilities(c->buf[c->cur], (int)c->amp, c->n, d_probs, c->d_partials,
                                  probabilities_partials_needed(), norm_out ? c->d_norms : nullptr,
                                  c->stream);
     if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
-    if (c->profiling) {
-        QSIM_CUDA(cudaEventRecord(c->ev[2 * prof0 + 1], c->stream), "cudaEventRecord");
-        c->prof_kinds.push_back(6);
-        c->prof_bytes.push_back((double)c->n * (double)(c->amp + (d_probs ? 8 : 0)));
-    }
+    int prc = prof_end(c, slot);
+    if (prc != QSIM_OK) return prc;
     if (norm_out) {
         int rc = check_device(c);
         if (rc != QSIM_OK) return rc;

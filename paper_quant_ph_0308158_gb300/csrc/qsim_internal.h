@@ -170,12 +170,15 @@ constexpr uint64_t kBatchItemOutputs = 16384;  // = 256 threads x 64 outputs
 // Message returned by qsim_last_error() on this host thread (qsim_api.cu).
 void set_last_error(const std::string &msg);
 
-// Kernel launchers (kernels.cu).  All return cudaError_t as int.
+// Kernel launchers (kernels.cu).  All return cudaError_t as int.  A non-null
+// d_probs makes a tile or gather pass also write the FP64 probabilities of
+// the state it leaves (2^M doubles).
 int launch_sweep(void *state, int amp_bytes, const SweepParams &p, int *d_err, void *stream);
 int launch_tile(void *state, int amp_bytes, const TilePass &p, const TileStep *d_steps,
-                int *d_err, void *stream);
+                int *d_err, double *d_probs, void *stream);
 int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &p,
-                  const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err, void *stream);
+                  const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err, double *d_probs,
+                  void *stream);
 int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d_probs,
                          double *d_partials, int n_partials, double *d_norm, void *stream);
 int probabilities_partials_needed();
@@ -195,7 +198,7 @@ size_t tile_smem_bytes(int amp_bytes, int k);
 int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *compile_ms,
                 std::string *msg);
 int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
-                      size_t n, void *stream, std::string *msg);
+                      size_t n, double *d_probs, void *stream, std::string *msg);
 int num_sms();
 
 }  // namespace qsim

@@ -1,10 +1,11 @@
 """Shared assertions for the GPU tests."""
 import numpy as np
 
-# FP64 probabilities: the contract is 1e-12 relative to the CPU oracle.  The
-# kernel evaluates re*re + im*im with one fused multiply-add, so it may
-# differ from the oracle's two separately rounded products by one unit in the
-# last place; anything beyond two units is a real error.
+# FP64 probabilities: the contract is 1e-12 relative to the CPU oracle.  For
+# complex128 the kernel evaluates re*re + im*im with one fused multiply-add,
+# so it may differ from the oracle's two separately rounded products by one
+# unit in the last place (complex64 squares are exact, so there the results
+# are identical); anything beyond two units is a real error.
 PROB_RTOL = 1e-12
 
 

@@ -1,8 +1,9 @@
 """GPU parity: the CUDA library through its C ABI against the CPU oracle.
 
 Amplitudes are only moved, so states must match bit for bit; FP64
-probabilities match the oracle bit for bit too (same two products and one
-sum, no FMA), and the norm within 1e-12 relative (summation order differs).
+probabilities match the oracle within 1e-12 relative and two units in the
+last place (bit for bit for complex64, whose squares are exact), and the norm
+within 1e-12 relative (summation order differs).
 Small cases compare every amplitude; the full-size workloads compare sampled
 output rows (the oracle evaluates them one at a time) plus permutation
 invariants of the whole state computed on the device.
@@ -173,6 +174,31 @@ def test_probabilities_fp64(dtype, M):
     assert abs(norm - 1.0) < 1e-6 if dtype == np.complex64 else abs(norm - 1.0) < 1e-12
 
 
+def test_complex64_probabilities_bit_identical_including_special_values():
+    """complex64 squares are exact in FP64, so the only rounding is the sum:
+    the device must agree with the oracle bit for bit, also for zeros of
+    either sign, subnormals, the largest and smallest normals, infinities
+    and NaNs (a state of 'arbitrary magnitude', Sec. 1)."""
+    M = 14
+    f32 = np.finfo(np.float32)
+    special = np.array([0.0, -0.0, 1.0, -1.5, f32.max, -f32.max, f32.tiny, -f32.tiny,
+                        f32.smallest_subnormal, 3 * f32.smallest_subnormal,
+                        np.float32(1e-40), np.inf, -np.inf, np.nan, 2.0 ** -75, 2.0 ** 63],
+                       dtype=np.float32)
+    rng = np.random.default_rng(11)
+    parts = rng.standard_normal(2 << M).astype(np.float32)
+    parts *= np.exp2(rng.integers(-140, 120, size=parts.size)).astype(np.float32)
+    parts[rng.integers(0, parts.size, size=4096)] = rng.choice(special, size=4096)
+    k1 = parts.view(np.complex64)
+    want = oracle.probabilities(k1)
+    with Simulator(M, np.complex64) as sim:
+        sim.load_state(k1)
+        got = sim.probabilities()
+    np.testing.assert_array_equal(got.view(np.uint64)[~np.isnan(want)],
+                                  want.view(np.uint64)[~np.isnan(want)])
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+
+
 # ----------------------------------------------------------------------------
 # full-size workloads
 # ----------------------------------------------------------------------------
@@ -256,6 +282,96 @@ def test_compiled_gather_bit_exact(dtype, M, L, seed):
         kernels = {k for k, _, _ in sim.pass_times()}
     np.testing.assert_array_equal(got, want)
     assert "qsim_jit_gather" in kernels
+
+
+# (strategy, jit, circuit) -> kernel of the last pass, which writes the probabilities
+FUSED_CASES = [
+    ("tile", False, "mixed", "tile_kernel"),
+    ("inplace", False, "mixed", "tile_kernel"),
+    ("gather", False, "cnot", "gather_affine_kernel"),
+    ("gather", False, "mixed", "gather_sliced_kernel"),
+    ("gather", True, "mixed", "qsim_jit_gather"),
+    ("sweep", False, "mixed", "probs_kernel"),  # a sweep cannot: separate pass
+]
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("strategy,jit,mix,kernel", FUSED_CASES)
+@pytest.mark.parametrize("M", [10, 17])  # compiled gathers start at M = 10
+def test_apply_circuit_probabilities(cuda, dtype, strategy, jit, mix, kernel, M):
+    """Probabilities written by the last pass equal the separate probability
+    pass bit for bit and the oracle's within the contract; the state is
+    bit-exact."""
+    torch = cuda
+    L = 120
+    seed = 70 + M
+    if mix == "cnot":
+        steps = W.cnot_circuit(M, L, seed)
+    else:
+        steps = W.random_circuit(M, L, seed, max_controls=min(5, M - 1))
+    k1 = W.random_state(M, dtype, seed)
+    want_state = oracle.apply_circuit(M, k1, steps)
+    want_p = oracle.probabilities(want_state.astype(dtype))
+    fused = torch.full((1 << M,), -1.0, dtype=torch.float64, device="cuda")
+    plain = torch.empty(1 << M, dtype=torch.float64, device="cuda")
+    with Simulator(M, dtype) as sim:
+        sim.set_strategy(strategy)
+        sim.set_jit(jit)
+        sim.set_canonicalize(False)
+        sim.set_profiling(True)
+        sim.load_state(k1)
+        sim.apply_probabilities(steps, fused.data_ptr())
+        kernels = [k for k, _, _ in sim.pass_times()]
+        got_state = sim.read_state()
+        sim.probabilities_device(plain.data_ptr())
+        sim.synchronize()
+    np.testing.assert_array_equal(got_state, want_state.astype(dtype))
+    assert kernels[-1] == kernel
+    assert kernels.count("probs_kernel") == (1 if kernel == "probs_kernel" else 0)
+    f = fused.cpu().numpy()
+    np.testing.assert_array_equal(f.view(np.uint64), plain.cpu().numpy().view(np.uint64))
+    if dtype == np.complex64:
+        np.testing.assert_array_equal(f.view(np.uint64), want_p.view(np.uint64))
+    else:
+        assert_probs_close(f, want_p)
+
+
+def test_apply_circuit_probabilities_idle_tiles_and_empty_circuit(cuda):
+    """A tile pass whose steps fire on a few tiles only must still write the
+    probabilities of every tile; an empty circuit runs the probability pass."""
+    torch = cuda
+    M = 18
+    # Toffoli and 3-control steps on low targets controlled by the top bits:
+    # most tiles have no active step
+    steps = W.make_steps([(0, (1 << 17) | (1 << 16), (1 << 17) | (1 << 16)),
+                          (3, (1 << 17) | (1 << 16) | (1 << 15), (1 << 17) | (1 << 16) | (1 << 15)),
+                          (1, 1 << 17, 0)])
+    for dtype in (np.complex64, np.complex128):
+        k1 = W.random_state(M, dtype, 5)
+        want_state = oracle.apply_circuit(M, k1, steps).astype(dtype)
+        want_p = oracle.probabilities(want_state)
+        for circuit, strategy in ((steps, "tile"), (steps[:0], "auto")):
+            out = torch.full((1 << M,), -1.0, dtype=torch.float64, device="cuda")
+            with Simulator(M, dtype) as sim:
+                sim.set_strategy(strategy)
+                sim.load_state(k1)
+                sim.apply_probabilities(circuit, out.data_ptr())
+                sim.synchronize()
+                state = sim.read_state()
+            ref_state = want_state if len(circuit) else k1
+            ref_p = want_p if len(circuit) else oracle.probabilities(k1)
+            np.testing.assert_array_equal(state, ref_state)
+            assert_probs_close(out.cpu().numpy(), ref_p)
+
+
+def test_apply_circuit_probabilities_rejects_bad_output(cuda):
+    torch = cuda
+    with Simulator(8, np.complex128) as sim:
+        buf = torch.empty(257, dtype=torch.float64, device="cuda")
+        with pytest.raises(QsimError):
+            sim.apply_probabilities(W.cnot_circuit(8, 4, 1), 0)
+        with pytest.raises(QsimError):
+            sim.apply_probabilities(W.cnot_circuit(8, 4, 1), buf.data_ptr() + 4)
 
 
 def test_wide_indices_m33():
