@@ -56,7 +56,9 @@ METRIC = "amplitude-steps/s"
 UNIT = "amp-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 CSRC = os.path.join(ROOT, "paper_quant_ph_0308158_gb300", "csrc")
-KERNEL_SOURCE = {"qsim_jit_gather": "jit.cu"}  # every other kernel lives in kernels.cu
+# source files that define a kernel's code (every other kernel: kernels.cu)
+KERNEL_SOURCE = {"qsim_jit_gather": ("jit.cu", "prob_math.cuh")}
+KERNELS_CU = ("kernels.cu", "prob_math.cuh", "qsim_internal.h")
 
 
 def workload(name: str):
@@ -184,10 +186,12 @@ def hbm_peak():
 
 
 def kernel_source_hash(kernel: str) -> str:
-    """First 16 hex digits of the SHA-256 of the source file of a kernel."""
-    path = os.path.join(CSRC, KERNEL_SOURCE.get(kernel, "kernels.cu"))
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the source files of a kernel."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCE.get(kernel, KERNELS_CU):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, wl: str):
@@ -276,13 +280,22 @@ def run_ours(args, rank, ws, local):
     tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
 
     # seeded state in pinned host memory (also the e2e input buffer), or the
-    # qubits of a product-state input generated on the device (App. 1)
+    # qubits of a product-state input generated on the device (App. 1); the
+    # end-to-end leg copies that state in from the host all the same
     qubits = cfg.get("qubits")
     h_in = None
-    if qubits is None:
+    if qubits is None or not args.no_e2e:
         h_in_t = torch.empty(n, dtype=tdt, pin_memory=True)
         h_in = h_in_t.numpy()
-        W.random_state(M, dtype, cfg["state_seed"], out=h_in)
+        if qubits is None:
+            W.random_state(M, dtype, cfg["state_seed"], out=h_in)
+        else:  # the only product-state workload is the Sec. 4 alternating input
+            assert np.array_equal(qubits, W.sec4_qubits(M)), "host copy of this product state"
+            W.alternating_state(M, dtype, out=h_in)
+    # pinned buffers for the end-to-end leg's probabilities, taken early
+    # (copies from pinned memory taken after host memory has churned can be
+    # far slower)
+    e2e_outs = None if args.no_e2e else torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
 
     def load_input():
         if qubits is None:
@@ -363,7 +376,7 @@ def run_ours(args, rank, ws, local):
         # Two contexts on two streams alternate steps, so one step's copies
         # overlap the other's kernels (each context waits for its previous
         # step before reusing its buffers).
-        h2d = n * amp if qubits is None else qubits.nbytes
+        h2d = n * amp
         d2h = n * 8
         s2 = torch.cuda.Stream()
         with torch.cuda.stream(s2):
@@ -374,7 +387,7 @@ def run_ours(args, rank, ws, local):
             sim2.set_jit(True)
         sims = (sim, sim2)
         streams = (stream, s2)
-        outs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        outs = [e2e_outs[:n], e2e_outs[n:]]
 
         loaded = [torch.cuda.Event() for _ in range(2)]
 
@@ -385,10 +398,7 @@ def run_ours(args, rank, ws, local):
                 sm.synchronize()  # this context's previous step is done
             if i >= 1:  # copies in go one after the other over the host link
                 streams[c].wait_event(loaded[1 - c])
-            if qubits is None:
-                sm.load_state_async(h_in)
-            else:
-                sm.load_product_state(qubits)
+            sm.load_state_async(h_in)
             loaded[c].record(streams[c])
             sm.apply(steps)
             sm.probabilities_async(outs[c].numpy())
@@ -590,9 +600,13 @@ def serve_plain_baseline(specs, pool):
     from paper_quant_ph_0308158_gb300 import Simulator
 
     sims, outs = {}, {}
-    for M in sorted({sp["M"] for sp in specs}):
+    ms = sorted({sp["M"] for sp in specs})
+    block = torch.empty(sum(1 << M for M in ms), dtype=torch.float64, pin_memory=True).numpy()
+    off = 0
+    for M in ms:
         sims[M] = Simulator(M, np.complex128)
-        outs[M] = torch.empty(1 << M, dtype=torch.float64, pin_memory=True).numpy()
+        outs[M] = block[off: off + (1 << M)]
+        off += 1 << M
     for sp in specs[:3]:  # warm-up
         sims[sp["M"]].load_state(pool[sp["M"]][1])
         sims[sp["M"]].apply(sp["steps"])
@@ -625,17 +639,29 @@ def run_serve(args, rank, ws, local):
     build.build()
     torch.cuda.set_device(local)
     m_hi = args.serve_m_max
-    specs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=5,
-                               m_range=(12, m_hi), l_range=(100, 5000), mix="cnot")
     dtype = np.dtype(np.complex128)
-    pool = {}
-    for M in sorted({sp["M"] for sp in specs}):
-        t = torch.empty(1 << M, dtype=torch.complex128, pin_memory=True)
+    # Input states: one pinned block, taken before anything else churns host
+    # memory and sliced per M.  Copies from pinned memory scattered over many
+    # small physical pieces ran at 25-45 GB/s instead of 211 GB/s on the
+    # GB300's host link, so a client should pin large blocks early.
+    sizes = {M: 1 << M for M in range(12, m_hi + 1)}
+    block = torch.empty(sum(sizes.values()) + 256 * len(sizes), dtype=torch.complex128,
+                        pin_memory=True)
+    pool, off = {}, 0
+    for M in sorted(sizes, reverse=True):
+        t = block[off: off + sizes[M]]
+        off += sizes[M] + 256
         W.random_state(M, dtype, 5000 + M, out=t.numpy())
         pool[M] = (t, t.numpy())
+    specs = W.serving_requests(n=args.serve_requests, rate=args.serve_rate, seed=5,
+                               m_range=(12, m_hi), l_range=(100, 5000), mix="cnot")
     budget = int(args.serve_budget_gb * 1e9)
     host_bytes = int(args.serve_host_gb * 1e9)
     srv = Server(budget, host_bytes, dtype)
+    srv.set_backfill(args.serve_backfill_ms)
+    srv.set_copy_streams(args.serve_copy_streams)
+    if args.serve_trace:
+        srv.set_tracing(True)
     lat = []
     amp_steps = 0.0
     done = 0
@@ -665,6 +691,10 @@ def run_serve(args, rank, ws, local):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     st = srv.stats()
+    if args.serve_trace:
+        tr = srv.trace()
+        np.savetxt(args.serve_trace, np.column_stack([tr[f] for f in tr.dtype.names]),
+                   delimiter=",", header=",".join(tr.dtype.names), comments="", fmt="%.6g")
     srv.close()
     lat_a = np.array(lat)
     value = amp_steps / wall
@@ -683,6 +713,14 @@ def run_serve(args, rank, ws, local):
                    "latency_ms_p99": float(np.percentile(lat_a, 99)),
                    "latency_ms_max": float(lat_a.max()), "wall_s": wall,
                    "rounds": st["rounds"], "peak_hbm_in_use": st["peak_in_use_bytes"],
+                   "backfill_ms": args.serve_backfill_ms, "backfilled": st["backfilled"],
+                   "copy_streams": args.serve_copy_streams,
+                   "h2d_gbs_while_busy": st["h2d_bytes"] / max(st["h2d_busy_ms"], 1e-9) / 1e6,
+                   "d2h_gbs_while_busy": st["d2h_bytes"] / max(st["d2h_busy_ms"], 1e-9) / 1e6,
+                   "h2d_busy_frac": st["h2d_busy_ms"] / (1e3 * wall),
+                   "d2h_busy_frac": st["d2h_busy_ms"] / (1e3 * wall),
+                   "compute_busy_frac": st["compute_busy_ms"] / (1e3 * wall),
+                   "copy_issue_ms_total": st["issue_ms"], "copy_issue_ms_max": st["issue_ms_max"],
                    "step": "one request (submit to FP64 probabilities in host memory)",
                    "plain": plain,
                    "served_over_plain": value / plain["value"] if plain else None},
@@ -713,6 +751,12 @@ def main():
     ap.add_argument("--serve-m-max", type=int, default=30)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-host-gb", type=float, default=48.0)
+    ap.add_argument("--serve-backfill-ms", type=float, default=100.0,
+                    help="admit later requests ahead of a head that waited less (-1: FIFO)")
+    ap.add_argument("--serve-copy-streams", type=int, default=2, choices=[1, 2],
+                    help="copies in and out on two overlapping streams or on one")
+    ap.add_argument("--serve-trace", default="",
+                    help="write a per-request timeline (CSV) of the serving run to this path")
     ap.add_argument("--serve-plain-requests", type=int, default=400,
                     help="requests timed one at a time for the plain comparison (0: skip)")
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")

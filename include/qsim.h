@@ -299,16 +299,21 @@ int qsim_batch_info(qsim_batch *b, qsim_batch_stats *out);
 /* A server accepts simulation requests at any time and keeps the GPU busy
  * with all of them (the paper has no counterpart).  Each request -- M, an
  * input state in host memory, a wiring diagram -- is validated and planned at
- * submission, then waits in FIFO order until its device memory (state,
- * scratch, FP64 probabilities, plan tables: 2 * amp + 8 bytes per amplitude
- * plus tables) fits in the server's HBM budget and its result fits in the
- * server's pinned host result arena.  A scheduler thread uploads admitted
- * states on a copy stream and runs rounds back to back: a round launches the
- * next pass of every request whose state is on the device as one persistent
- * launch, so requests that arrive while others run join the next round.
- * After its last pass a request's probabilities are computed and copied into
- * the result arena on a second copy stream, and its device memory returns to
- * the budget.  All steps are applied (no cancellation). */
+ * submission, then waits in arrival order (with bounded backfill, see
+ * qsim_server_set_backfill) until its device memory fits in the server's HBM
+ * budget, its result fits in the server's pinned host result arena, and the
+ * uploads already queued are short (under 8 GiB).  Device memory is two
+ * blocks: the input state plus plan tables (amp bytes per amplitude), and a
+ * second buffer of amp bytes per amplitude when the plan has more than one
+ * gather pass, else of 8.  A scheduler thread uploads admitted states on a
+ * copy stream and runs rounds back to back: a round launches the next pass
+ * of every request whose state is on the device as one persistent launch,
+ * so requests that arrive while others run join the next round.  The last
+ * gather pass writes only the FP64 probabilities (the served result), into
+ * the buffer it does not read; then the other block returns to the budget,
+ * the probabilities are copied into the result arena on a second copy
+ * stream, and their block returns after the copy.  All steps are applied (no
+ * cancellation). */
 typedef struct qsim_server qsim_server;
 
 typedef struct qsim_server_stats {
@@ -321,6 +326,15 @@ typedef struct qsim_server_stats {
     uint64_t peak_in_use_bytes;
     uint64_t host_in_use_bytes; /* result arena bytes held by unreleased results */
     double amplitude_steps;     /* sum over completed requests of 2^M * L       */
+    uint64_t backfilled;        /* requests admitted ahead of the queue's head  */
+    uint64_t h2d_bytes;         /* states copied in                             */
+    uint64_t d2h_bytes;         /* probabilities copied out                     */
+    double h2d_busy_ms;         /* summed durations of the state copies in and  */
+    double d2h_busy_ms;         /* of the result copies out (completed requests) */
+    double compute_busy_ms;     /* summed durations of the request-pass rounds  */
+    double issue_ms, issue_ms_max; /* host time spent issuing the copies (total,
+                                      longest): a copy from host memory that is
+                                      not pinned runs while it is issued */
 } qsim_server_stats;
 
 /* Reserve hbm_budget_bytes of device memory (one cudaMalloc) and a pinned
@@ -353,7 +367,47 @@ int qsim_server_release(qsim_server *s, uint64_t req_id);
 /* Block until no request is waiting or running (QSIM_ETIMEOUT after timeout_s). */
 int qsim_server_wait_all(qsim_server *s, double timeout_s);
 
+/* Admission policy.  Requests are admitted in arrival order; while the
+ * oldest waiting request does not fit and has waited less than
+ * max_head_wait_ms, later requests that fit are admitted ahead of it
+ * (backfill, default 100 ms).  After that nothing passes it, so the budget
+ * drains until it fits.  A negative value disables backfill (strict FIFO). */
+int qsim_server_set_backfill(qsim_server *s, double max_head_wait_ms);
+
+/* Copies in and out on two streams that overlap (n = 2, default) or on one
+ * stream (n = 1).  QSIM_EBUSY while requests are running. */
+int qsim_server_set_copy_streams(qsim_server *s, int n);
+
+/* Pause (paused != 0) or resume admission.  While paused, submitted requests
+ * wait and admitted ones run to completion; e.g. to submit a group of
+ * requests that should be admitted together. */
+int qsim_server_set_paused(qsim_server *s, int paused);
+
 int qsim_server_get_stats(qsim_server *s, qsim_server_stats *out);
+
+/* Timeline of one finished request, in milliseconds since tracing was
+ * switched on: host clock for submit/admit/done, device events for the
+ * copies (start = when the copy stream reached the copy).  A device time
+ * that could not be read is -1. */
+typedef struct qsim_server_trace_record {
+    uint64_t id;
+    uint32_t M;
+    uint32_t passes;
+    uint64_t L;
+    double submit_ms, admit_ms;
+    double upload_start_ms, upload_end_ms;     /* state and tables in  */
+    double compute_start_ms, compute_end_ms;   /* rounds with its passes (-1: none) */
+    double download_start_ms, download_end_ms; /* probabilities out   */
+    double done_ms;                            /* seen complete       */
+} qsim_server_trace_record;
+
+/* Switch per-request tracing on (clears the record and sets the time
+ * origin) or off.  At most 2^22 records are kept. */
+int qsim_server_set_tracing(qsim_server *s, int enable);
+
+/* Move up to cap trace records (completion order) into out; *n_out gets
+ * how many.  Returned records are removed from the server's record. */
+int qsim_server_get_trace(qsim_server *s, qsim_server_trace_record *out, size_t cap, size_t *n_out);
 
 /* Stop the scheduler, wait for queued GPU work and free everything. */
 void qsim_server_destroy(qsim_server *s);

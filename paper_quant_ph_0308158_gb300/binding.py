@@ -52,7 +52,9 @@ EXPORTS = (
     "qsim_batch_load_state", "qsim_batch_read_state", "qsim_batch_state_device", "qsim_batch_run",
     "qsim_batch_run_plain", "qsim_batch_synchronize", "qsim_batch_info", "qsim_server_create",
     "qsim_server_submit", "qsim_server_poll", "qsim_server_release", "qsim_server_wait_all",
-    "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain",
+    "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain", "qsim_server_set_backfill",
+    "qsim_server_set_paused", "qsim_server_set_tracing", "qsim_server_get_trace",
+    "qsim_server_set_copy_streams",
 )
 
 
@@ -88,10 +90,23 @@ class ServerStats(ctypes.Structure):
                 ("launches", ctypes.c_uint64), ("active", ctypes.c_uint64),
                 ("waiting", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
                 ("in_use_bytes", ctypes.c_uint64), ("peak_in_use_bytes", ctypes.c_uint64),
-                ("host_in_use_bytes", ctypes.c_uint64), ("amplitude_steps", ctypes.c_double)]
+                ("host_in_use_bytes", ctypes.c_uint64), ("amplitude_steps", ctypes.c_double),
+                ("backfilled", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64), ("h2d_busy_ms", ctypes.c_double),
+                ("d2h_busy_ms", ctypes.c_double), ("compute_busy_ms", ctypes.c_double),
+                ("issue_ms", ctypes.c_double), ("issue_ms_max", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerTraceRecord(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("M", ctypes.c_uint32), ("passes", ctypes.c_uint32),
+                ("L", ctypes.c_uint64), ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("upload_start_ms", ctypes.c_double), ("upload_end_ms", ctypes.c_double),
+                ("compute_start_ms", ctypes.c_double), ("compute_end_ms", ctypes.c_double),
+                ("download_start_ms", ctypes.c_double), ("download_end_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -156,6 +171,11 @@ def load() -> ctypes.CDLL:
             "qsim_server_drain": ([p, p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_server_wait_all": ([p, ctypes.c_double], i),
             "qsim_server_get_stats": ([p, ctypes.POINTER(ServerStats)], i),
+            "qsim_server_set_backfill": ([p, ctypes.c_double], i),
+            "qsim_server_set_paused": ([p, i], i),
+            "qsim_server_set_copy_streams": ([p, i], i),
+            "qsim_server_set_tracing": ([p, i], i),
+            "qsim_server_get_trace": ([p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_server_destroy": ([p], None),
             "qsim_last_error": ([], ctypes.c_char_p),
             "qsim_version": ([], ctypes.c_char_p),
@@ -486,6 +506,40 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def set_backfill(self, max_head_wait_ms: float):
+        """Backfill admission while the oldest waiting request has waited less
+        than max_head_wait_ms (negative: strict FIFO)."""
+        _check(self._lib.qsim_server_set_backfill(self._s, float(max_head_wait_ms)))
+
+    def set_copy_streams(self, n: int):
+        """Copies in and out on two overlapping streams (2) or one stream (1)."""
+        _check(self._lib.qsim_server_set_copy_streams(self._s, int(n)))
+
+    def set_paused(self, paused: bool):
+        """Pause or resume admission (admitted requests keep running)."""
+        _check(self._lib.qsim_server_set_paused(self._s, int(bool(paused))))
+
+    def set_tracing(self, enable: bool):
+        """Record a timeline per finished request (see trace())."""
+        _check(self._lib.qsim_server_set_tracing(self._s, int(bool(enable))))
+
+    def trace(self) -> np.ndarray:
+        """Timelines recorded since the last call, as a structured array with
+        the fields of qsim_server_trace_record (milliseconds)."""
+        rows = []
+        while True:
+            buf = (ServerTraceRecord * 4096)()
+            n = ctypes.c_size_t(0)
+            _check(self._lib.qsim_server_get_trace(self._s, buf, 4096, ctypes.byref(n)))
+            rows.extend(buf[:n.value])
+            if n.value < 4096:
+                break
+        dt = np.dtype([(f, np.uint64 if t in (ctypes.c_uint64,) else
+                        np.uint32 if t is ctypes.c_uint32 else np.float64)
+                       for f, t in ServerTraceRecord._fields_])
+        return np.array([tuple(getattr(r, f) for f, _ in ServerTraceRecord._fields_) for r in rows],
+                        dtype=dt)
 
     def submit(self, M: int, k1: np.ndarray, steps) -> int:
         """k1 must stay alive and unchanged until the request is done (kept here)."""

@@ -443,7 +443,7 @@ __device__ __forceinline__ void affine_range(const char *__restrict__ in, char *
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (idx[u] < o1) {
-                dst[idx[u]] = v[u];
+                if (dst) dst[idx[u]] = v[u];  // no destination: probabilities only
                 if (probs) probs[idx[u]] = amp_prob(v[u]);
             }
     }
@@ -619,7 +619,7 @@ __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (o[u] < n) {
-                        dst[o[u]] = v[u];
+                        if (dst) dst[o[u]] = v[u];  // no destination: probabilities only
                         if (probs) probs[o[u]] = amp_prob(v[u]);
                     }
             }
@@ -708,10 +708,10 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__rest
                 if (threadIdx.x == 0) s_tables = (int32_t)item.pass;
             }
             affine_range<B, WIDE, I>(P.in, P.out, item.start + threadIdx.x, o1, kThreads, tab,
-                                     P.nbytes, P.bvec, nullptr);
+                                     P.nbytes, P.bvec, P.probs);
         } else if (P.kind == 4) {
             if (threadIdx.x == 0) s_tables = -1;
-            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem, nullptr);
+            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem, P.probs);
         } else {
             sweep_range<B>(P.out, P.sweep, item.start + threadIdx.x, o1, kThreads);
         }

@@ -147,7 +147,7 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
 // One circuit's pass inside a batched launch (batch.cu builds them).
 struct BatchPass {
     const char *in;        // gather source (unused by sweeps)
-    char *out;             // gather destination / sweep state
+    char *out;             // gather destination (NULL: probabilities only) / sweep state
     uint32_t M;
     uint32_t kind;         // 1 sweep, 3 affine gather, 4 bit-sliced gather
     uint32_t nbytes;       // affine: table bytes
@@ -155,6 +155,7 @@ struct BatchPass {
     uint64_t bvec;         // affine: constant term
     const uint64_t *tables;       // affine tables (device)
     const SlicedStep *steps;      // bit-sliced steps (device)
+    double *probs;                // gathers: non-null = also write FP64 probabilities
     SweepParams sweep;
 };
 // A work item: outputs (or sweep pairs) [start, start + count) of one pass;

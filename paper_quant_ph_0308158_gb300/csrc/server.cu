@@ -1,19 +1,22 @@
 // server.cu -- a request loop that serves circuit simulations continuously.
 //
 // Requests (M, input state, wiring diagram) are validated and planned when
-// they are submitted, then wait in FIFO order for admission.  A request is
-// admitted when its device memory (state + scratch + FP64 probabilities +
-// plan tables) fits in the server's HBM budget -- one cudaMalloc made at
-// creation and managed by a first-fit allocator -- and its result fits in the
-// pinned host result arena.  Admitted requests upload their state on a copy
-// stream.  A scheduler thread runs rounds back to back: each round takes the
-// next pass of every request whose state is on the device and launches them
-// all as one persistent batch_kernel level (the kernel of qsim_batch), so
-// requests that arrive while others run join at the next round and their
-// work overlaps on the device.  After its last pass a request's probabilities
-// are computed, copied to the host arena on a second copy stream, and its
-// device memory is returned to the budget.  The paper has no counterpart: it
-// runs one circuit at a time.
+// they are submitted, then wait in FIFO order for admission (with bounded
+// backfill, see admit()).  A request is admitted when its two device blocks
+// (input state + plan tables; a second buffer sized for what the plan writes
+// there) fit in the server's HBM budget -- one cudaMalloc made at creation
+// and managed by a first-fit allocator -- its result fits in the pinned host
+// result arena, and the uploads already queued are short.  Admitted requests
+// upload their state on a copy stream.  A scheduler thread runs rounds back
+// to back: each round takes the next pass of every request whose state is
+// on the device and launches them all as one persistent batch_kernel level
+// (the kernel of qsim_batch), so requests that arrive while others run join
+// at the next round and their work overlaps on the device.  A request's last
+// gather pass writes only the FP64 probabilities of its result (the served
+// output), into the buffer it does not read; the other block then returns to
+// the budget, the probabilities are copied to the host arena on a second
+// copy stream, and their block returns after the copy.  The paper has no
+// counterpart: it runs one circuit at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,18 +107,28 @@ struct Request {
     const void *host_in = nullptr;
     Plan plan;
     uint64_t L = 0;
-    // device layout inside the arena
-    size_t dev_off = 0, host_off = 0;
+    // device memory: two arena blocks.  Block 0 holds the input state buf[0]
+    // and the plan tables, block 1 the second buffer buf[1], sized for what
+    // the plan writes there (a state for a gather pass that is not the last,
+    // else only the probabilities).  The probabilities go to the buffer the
+    // last pass does not read; once they are written the other block is
+    // returned to the budget, and the probabilities' block after the copy out.
+    size_t off[2] = {0, 0}, bytes[2] = {0, 0};
+    bool held[2] = {false, false};
+    size_t host_off = 0;
     char *buf[2] = {nullptr, nullptr};
-    double *d_probs = nullptr;
     char *d_tab = nullptr;   // affine tables then sliced steps
     size_t sl_off = 0;       // byte offset of the sliced steps in d_tab
     int cur = 0;
     size_t next_pass = 0;
-    enum State { kWaiting, kUploading, kRunning, kFinishing, kDone } state = kWaiting;
-    cudaEvent_t uploaded = nullptr, finished = nullptr;
+    bool probs_fused = false;  // the last pass writes the probabilities (and no state)
+    int probs_buf = -1;        // buffer holding the probabilities
+    double compute_start_ms = -1, compute_end_ms = -1;  // rounds that ran its passes (trace)
+    enum State { kWaiting, kUploading, kRunning, kComputing, kFinishing, kDone } state = kWaiting;
+    cudaEvent_t uploaded = nullptr, computed = nullptr, finished = nullptr;
+    cudaEvent_t up0 = nullptr, down0 = nullptr;  // timing: starts of the two copies
     Clock::time_point t_submit, t_admit, t_done;
-    size_t dev_bytes = 0, host_bytes = 0;
+    size_t host_bytes = 0;
 };
 
 }  // namespace
@@ -129,7 +142,6 @@ struct qsim_server {
     Arena dev, host;
     cudaStream_t compute = nullptr, h2d = nullptr, d2h = nullptr;
     double *d_partials = nullptr, *d_norms = nullptr;
-    cudaEvent_t probs_ready = nullptr;
     int device = 0;
     // per-round device descriptors: a ring of slots
     static constexpr int kSlots = 4;
@@ -140,9 +152,18 @@ struct qsim_server {
         BatchItem *h_items = nullptr;
         size_t cap_passes = 0, cap_items = 0;
         uint32_t *d_counter = nullptr;
-        cudaEvent_t done = nullptr;
+        cudaEvent_t start = nullptr, done = nullptr;  // timing events around the round
         bool busy = false;
+        std::vector<std::shared_ptr<Request>> members;  // requests with a pass in the round
     } slots[kSlots];
+    double max_head_wait_ms = 100.0;  // backfill admission while the head waited less
+    size_t pending_upload_bytes = 0;  // admitted states not yet on the device
+    int copy_streams = 2;             // 2: copies in and out overlap; 1: one copy stream
+    cudaEvent_t t0_event = nullptr;   // device-time origin of the trace
+    Clock::time_point t0;             // host-time origin of the trace
+    bool tracing = false;
+    std::vector<qsim_server_trace_record> trace;
+    bool paused = false;              // admission paused (running requests continue)
     int slot_next = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -170,59 +191,142 @@ size_t tables_bytes(const Plan &p, size_t *sl_off)
     return t + align256(p.sliced_steps.size() * sizeof(SlicedStep));
 }
 
-// Try to admit the head of the queue; called with the lock held.
-bool admit_one(qsim_server *s)
+// Bytes of the two device blocks of a request (see Request): follow the
+// plan's ping-pong and record the largest write into each buffer.
+void block_sizes(const Plan &p, uint32_t M, size_t amp, size_t out[2])
 {
-    if (s->waiting.empty()) return false;
-    auto r = s->waiting.front();
+    const size_t n = 1ull << M;
+    size_t need[2] = {n * amp, n * 8};
+    int cur = 0;
+    for (size_t i = 0; i < p.passes.size(); ++i) {
+        if (p.passes[i].kind == kSweep) continue;  // in place
+        if (i + 1 < p.passes.size()) need[1 - cur] = std::max(need[1 - cur], n * amp);
+        cur = 1 - cur;
+    }
+    size_t sl = 0;
+    out[0] = align256(need[0]) + tables_bytes(p, &sl);
+    out[1] = align256(need[1]);
+}
+
+// Admitted states whose upload has not finished, in bytes, above which no
+// further request is admitted (about 40 ms of the host link).
+constexpr size_t kMaxPendingUpload = 8ull << 30;
+
+// Try to admit waiting request r; called with the lock held.
+bool try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
+{
     const size_t n = 1ull << r->M;
+    // a request is admitted when the uploads already queued are short, so
+    // that its memory is not held while it waits for the copy stream
+    if (s->pending_upload_bytes >= kMaxPendingUpload) return false;
     size_t sl_off = 0;
     const size_t tb = tables_bytes(r->plan, &sl_off);
-    r->dev_bytes = align256(n * s->amp) * 2 + align256(n * 8) + tb;
-    r->host_bytes = align256(n * 8);
-    size_t doff = 0, hoff = 0;
-    if (!s->dev.alloc(r->dev_bytes, &doff)) return false;
-    if (!s->host.alloc(r->host_bytes, &hoff)) {
-        s->dev.release(doff);
+    block_sizes(r->plan, r->M, s->amp, r->bytes);
+    // result probabilities, then a pinned copy of the plan tables: a copy
+    // from pageable memory would hold this thread until the copy stream
+    // reached it
+    r->host_bytes = align256(n * 8) + tb;
+    size_t hoff = 0;
+    if (!s->dev.alloc(r->bytes[0], &r->off[0])) return false;
+    if (!s->dev.alloc(r->bytes[1], &r->off[1])) {
+        s->dev.release(r->off[0]);
         return false;
     }
-    s->waiting.pop_front();
-    r->dev_off = doff;
+    if (!s->host.alloc(r->host_bytes, &hoff)) {
+        s->dev.release(r->off[0]);
+        s->dev.release(r->off[1]);
+        return false;
+    }
+    r->held[0] = r->held[1] = true;
     r->host_off = hoff;
-    char *base = s->d_arena + doff;
-    r->buf[0] = base;
-    r->buf[1] = base + align256(n * s->amp);
-    r->d_probs = reinterpret_cast<double *>(base + 2 * align256(n * s->amp));
-    r->d_tab = base + 2 * align256(n * s->amp) + align256(n * 8);
+    r->buf[0] = s->d_arena + r->off[0];
+    r->buf[1] = s->d_arena + r->off[1];
+    r->d_tab = r->buf[0] + align256(n * s->amp);
     r->sl_off = sl_off;
     r->t_admit = Clock::now();
     // upload state and tables on the copy stream
-    cudaMemcpyAsync(r->buf[0], r->host_in, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
+    char *h_tab = s->h_arena + hoff + align256(n * 8);
     if (!r->plan.gather_tables.empty())
-        cudaMemcpyAsync(r->d_tab, r->plan.gather_tables.data(),
-                        r->plan.gather_tables.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s->h2d);
+        std::memcpy(h_tab, r->plan.gather_tables.data(), r->plan.gather_tables.size() * sizeof(uint64_t));
     if (!r->plan.sliced_steps.empty())
-        cudaMemcpyAsync(r->d_tab + sl_off, r->plan.sliced_steps.data(),
-                        r->plan.sliced_steps.size() * sizeof(SlicedStep), cudaMemcpyHostToDevice, s->h2d);
+        std::memcpy(h_tab + sl_off, r->plan.sliced_steps.data(),
+                    r->plan.sliced_steps.size() * sizeof(SlicedStep));
+    cudaEventRecord(r->up0, s->h2d);
+    const auto e0 = Clock::now();
+    cudaMemcpyAsync(r->buf[0], r->host_in, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
+    if (tb) cudaMemcpyAsync(r->d_tab, h_tab, tb, cudaMemcpyHostToDevice, s->h2d);
+    // a copy from memory the driver does not see as pinned runs on this
+    // thread (and stalls the scheduler): record how long issuing took
+    const double enq = std::chrono::duration<double, std::milli>(Clock::now() - e0).count();
+    s->st.issue_ms += enq;
+    s->st.issue_ms_max = std::max(s->st.issue_ms_max, enq);
     cudaEventRecord(r->uploaded, s->h2d);
+    s->st.h2d_bytes += n * s->amp;
+    s->pending_upload_bytes += n * s->amp;
     r->state = Request::kUploading;
     s->active.push_back(r);
     ++s->st.admitted;
     return true;
 }
 
-// Queue the FP64 probabilities of a request whose passes are all queued, and
-// their copy into the host result arena.
+// Admission: FIFO, except that while the head of the queue does not fit and
+// has waited less than max_head_wait_ms, later requests that fit are admitted
+// ahead of it (backfill); after that nothing passes the head, so the budget
+// drains until it fits.  Called with the lock held.
+void admit(qsim_server *s)
+{
+    constexpr size_t kWindow = 256;  // requests looked at behind the head
+    if (s->paused) return;
+    while (!s->waiting.empty() && try_admit(s, s->waiting.front())) s->waiting.pop_front();
+    if (s->waiting.empty() || s->max_head_wait_ms < 0) return;
+    const double head_wait =
+        std::chrono::duration<double, std::milli>(Clock::now() - s->waiting.front()->t_submit).count();
+    if (head_wait >= s->max_head_wait_ms) return;
+    size_t looked = 0;
+    for (auto it = std::next(s->waiting.begin()); it != s->waiting.end() && looked < kWindow; ++looked) {
+        if (try_admit(s, *it)) {
+            ++s->st.backfilled;
+            it = s->waiting.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Queue the FP64 probabilities of a request whose passes are all queued (the
+// copy out is queued once they are written, see start_download).
 void finish_request(qsim_server *s, const std::shared_ptr<Request> &r)
 {
     const uint64_t n = 1ull << r->M;
-    launch_probabilities(r->buf[r->cur], (int)s->amp, n, r->d_probs, s->d_partials,
-                         probabilities_partials_needed(), nullptr, s->compute);
-    s->st.launches += 1;
-    cudaEventRecord(s->probs_ready, s->compute);
-    cudaStreamWaitEvent(s->d2h, s->probs_ready, 0);
-    cudaMemcpyAsync(s->h_arena + r->host_off, r->d_probs, n * 8, cudaMemcpyDeviceToHost, s->d2h);
-    cudaEventRecord(r->finished, s->d2h);
+    if (!r->probs_fused) {  // the final state is in buf[cur]; the other buffer is free
+        r->probs_buf = 1 - r->cur;
+        launch_probabilities(r->buf[r->cur], (int)s->amp, n,
+                             reinterpret_cast<double *>(r->buf[r->probs_buf]), s->d_partials,
+                             probabilities_partials_needed(), nullptr, s->compute);
+        s->st.launches += 1;
+    }
+    cudaEventRecord(r->computed, s->compute);
+    r->state = Request::kComputing;
+}
+
+// The probabilities are written: return the other block to the budget and
+// queue their copy into the host result arena.  Queued only now, so that a
+// copy stream shared with the uploads never waits on the compute stream.
+void start_download(qsim_server *s, const std::shared_ptr<Request> &r)
+{
+    const uint64_t n = 1ull << r->M;
+    const int other = 1 - r->probs_buf;
+    s->dev.release(r->off[other]);
+    r->held[other] = false;
+    cudaStream_t st = s->copy_streams == 1 ? s->h2d : s->d2h;
+    cudaEventRecord(r->down0, st);
+    const auto e0 = Clock::now();
+    cudaMemcpyAsync(s->h_arena + r->host_off, r->buf[r->probs_buf], n * 8, cudaMemcpyDeviceToHost, st);
+    const double enq = std::chrono::duration<double, std::milli>(Clock::now() - e0).count();
+    s->st.issue_ms += enq;
+    s->st.issue_ms_max = std::max(s->st.issue_ms_max, enq);
+    s->st.d2h_bytes += n * 8;
+    cudaEventRecord(r->finished, st);
     r->state = Request::kFinishing;
 }
 
@@ -252,16 +356,14 @@ int ensure_slot(qsim_server::Slot &sl, size_t np, size_t ni)
 bool run_round(qsim_server *s, std::vector<std::shared_ptr<Request>> &ready)
 {
     qsim_server::Slot &sl = s->slots[s->slot_next];
-    if (sl.busy) {
-        if (cudaEventQuery(sl.done) != cudaSuccess) return false;  // ring full: wait
-        sl.busy = false;
-    }
+    if (sl.busy) return false;  // ring full: wait for the oldest round
     std::vector<BatchPass> passes;
     std::vector<BatchItem> items;
     uint32_t max_sliced_M = 0;
     bool wide = false;
     for (auto &r : ready) {
         const Pass &p = r->plan.passes[r->next_pass];
+        const bool last = r->next_pass + 1 == r->plan.passes.size();
         BatchPass bp{};
         bp.M = r->M;
         if (r->M > 32) wide = true;
@@ -271,21 +373,26 @@ bool run_round(qsim_server *s, std::vector<std::shared_ptr<Request>> &ready)
             bp.out = r->buf[r->cur];
             bp.sweep = p.sweep;
             units = p.sweep.n_pairs;
-        } else if (p.gather.affine) {
-            bp.kind = 3;
-            bp.in = r->buf[r->cur];
-            bp.out = r->buf[1 - r->cur];
-            bp.nbytes = p.gather.nbytes;
-            bp.bvec = p.gather.bvec;
-            bp.tables = reinterpret_cast<const uint64_t *>(r->d_tab) + p.gather.table_off;
-            r->cur = 1 - r->cur;
         } else {
-            bp.kind = 4;
             bp.in = r->buf[r->cur];
             bp.out = r->buf[1 - r->cur];
-            bp.nsteps = p.gather.nsteps;
-            bp.steps = reinterpret_cast<const SlicedStep *>(r->d_tab + r->sl_off) + p.gather.step_off;
-            max_sliced_M = std::max(max_sliced_M, r->M);
+            if (p.gather.affine) {
+                bp.kind = 3;
+                bp.nbytes = p.gather.nbytes;
+                bp.bvec = p.gather.bvec;
+                bp.tables = reinterpret_cast<const uint64_t *>(r->d_tab) + p.gather.table_off;
+            } else {
+                bp.kind = 4;
+                bp.nsteps = p.gather.nsteps;
+                bp.steps = reinterpret_cast<const SlicedStep *>(r->d_tab + r->sl_off) + p.gather.step_off;
+                max_sliced_M = std::max(max_sliced_M, r->M);
+            }
+            if (last) {  // only the probabilities of the result are served: no state is stored
+                bp.probs = reinterpret_cast<double *>(bp.out);
+                bp.out = nullptr;
+                r->probs_buf = 1 - r->cur;
+                r->probs_fused = true;
+            }
             r->cur = 1 - r->cur;
         }
         const uint32_t pid = (uint32_t)passes.size();
@@ -303,11 +410,13 @@ bool run_round(qsim_server *s, std::vector<std::shared_ptr<Request>> &ready)
     cudaMemcpyAsync(sl.d_passes, sl.h_passes, passes.size() * sizeof(BatchPass), cudaMemcpyHostToDevice, s->compute);
     cudaMemcpyAsync(sl.d_items, sl.h_items, items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s->compute);
     cudaMemsetAsync(sl.d_counter, 0, sizeof(uint32_t), s->compute);
+    cudaEventRecord(sl.start, s->compute);
     int e = launch_batch_level((int)s->amp, wide, sl.d_passes, sl.d_items, (uint32_t)items.size(),
                                sl.d_counter, batch_smem_bytes(max_sliced_M), s->compute);
     if (e != cudaSuccess) s->worker_error = std::string("round launch: ") + cudaGetErrorString((cudaError_t)e);
     cudaEventRecord(sl.done, s->compute);
     sl.busy = true;
+    if (s->tracing) sl.members = ready;
     s->slot_next = (s->slot_next + 1) % qsim_server::kSlots;
     ++s->st.rounds;
     ++s->st.launches;
@@ -315,6 +424,60 @@ bool run_round(qsim_server *s, std::vector<std::shared_ptr<Request>> &ready)
     for (auto &r : ready)
         if (r->next_pass == r->plan.passes.size()) finish_request(s, r);
     return true;
+}
+
+constexpr size_t kMaxTrace = 1u << 22;
+
+double host_ms(const qsim_server *s, Clock::time_point t)
+{
+    return std::chrono::duration<double, std::milli>(t - s->t0).count();
+}
+
+double dev_ms(const qsim_server *s, cudaEvent_t e)
+{
+    float ms = 0.f;
+    return cudaEventElapsedTime(&ms, s->t0_event, e) == cudaSuccess ? (double)ms : -1.0;
+}
+
+// One finished request's timeline (host and device clocks share the origin
+// taken when tracing was switched on).  Called with the lock held.
+void record_trace(qsim_server *s, const Request &r)
+{
+    qsim_server_trace_record t{};
+    t.id = r.id;
+    t.M = r.M;
+    t.passes = (uint32_t)r.plan.passes.size();
+    t.L = r.L;
+    t.submit_ms = host_ms(s, r.t_submit);
+    t.admit_ms = host_ms(s, r.t_admit);
+    t.upload_start_ms = dev_ms(s, r.up0);
+    t.upload_end_ms = dev_ms(s, r.uploaded);
+    t.compute_start_ms = r.compute_start_ms;
+    t.compute_end_ms = r.compute_end_ms;
+    t.download_start_ms = dev_ms(s, r.down0);
+    t.download_end_ms = dev_ms(s, r.finished);
+    t.done_ms = host_ms(s, r.t_done);
+    s->trace.push_back(t);
+}
+
+// Retire finished rounds: their descriptor slots become free and their
+// durations are added to the compute time.  Called with the lock held.
+void retire_rounds(qsim_server *s)
+{
+    for (auto &sl : s->slots) {
+        if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sl.start, sl.done) == cudaSuccess) s->st.compute_busy_ms += ms;
+        if (s->tracing) {
+            const double a = dev_ms(s, sl.start), b = dev_ms(s, sl.done);
+            for (auto &r : sl.members) {
+                if (r->compute_start_ms < 0) r->compute_start_ms = a;
+                r->compute_end_ms = b;
+            }
+        }
+        sl.members.clear();
+        sl.busy = false;
+    }
 }
 
 void worker_loop(qsim_server *s)
@@ -325,14 +488,24 @@ void worker_loop(qsim_server *s)
         bool launched = false, idle = true;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            // completions free memory first
+            retire_rounds(s);
+            // completions free memory first: the block without the
+            // probabilities once they are written, the rest after the copy out
             for (auto it = s->active.begin(); it != s->active.end();) {
                 auto &r = *it;
+                if (r->state == Request::kComputing && cudaEventQuery(r->computed) == cudaSuccess)
+                    start_download(s, r);
                 if (r->state == Request::kFinishing && cudaEventQuery(r->finished) == cudaSuccess) {
                     r->t_done = Clock::now();
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, r->up0, r->uploaded) == cudaSuccess) s->st.h2d_busy_ms += ms;
+                    if (cudaEventElapsedTime(&ms, r->down0, r->finished) == cudaSuccess) s->st.d2h_busy_ms += ms;
+                    if (s->tracing && s->trace.size() < kMaxTrace) record_trace(s, *r);
                     r->state = Request::kDone;
                     s->completions.push_back(r->id);
-                    s->dev.release(r->dev_off);
+                    for (int b = 0; b < 2; ++b)
+                        if (r->held[b]) s->dev.release(r->off[b]);
+                    r->held[0] = r->held[1] = false;
                     ++s->st.completed;
                     s->st.amplitude_steps += (double)(1ull << r->M) * (double)r->L;
                     it = s->active.erase(it);
@@ -341,11 +514,12 @@ void worker_loop(qsim_server *s)
                     ++it;
                 }
             }
-            while (admit_one(s)) {
-            }
+            retire_rounds(s);  // after the completions: their rounds are done
+            admit(s);
             for (auto &r : s->active) {
                 if (r->state == Request::kUploading && cudaEventQuery(r->uploaded) == cudaSuccess) {
                     r->state = Request::kRunning;
+                    s->pending_upload_bytes -= (1ull << r->M) * s->amp;
                     if (r->plan.passes.empty()) finish_request(s, r);  // nothing to apply
                 }
                 if (r->state == Request::kRunning && r->next_pass < r->plan.passes.size())
@@ -392,7 +566,6 @@ int qsim_server_create(size_t hbm_budget_bytes, size_t host_result_bytes, int dt
     s->dev.init(hbm_budget_bytes);
     s->host.init(host_result_bytes);
     cudaGetDevice(&s->device);
-    cudaEventCreateWithFlags(&s->probs_ready, cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
@@ -400,7 +573,8 @@ int qsim_server_create(size_t hbm_budget_bytes, size_t host_result_bytes, int dt
     cudaMalloc(&s->d_norms, sizeof(double));
     for (auto &sl : s->slots) {
         cudaMalloc(&sl.d_counter, sizeof(uint32_t));
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        cudaEventCreate(&sl.start);
+        cudaEventCreate(&sl.done);
     }
     s->st.budget_bytes = hbm_budget_bytes;
     s->worker = std::thread(worker_loop, s);
@@ -422,16 +596,20 @@ int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const 
     int rc = make_plan(M, steps, L, o, &r->plan, &msg);
     if (rc != QSIM_OK) return sfail(rc, msg);
     const size_t n = 1ull << M;
-    size_t sl_off = 0;
-    const size_t need = align256(n * s->amp) * 2 + align256(n * 8) + tables_bytes(r->plan, &sl_off);
-    if (need > s->dev.size() || align256(n * 8) > s->host.size())
+    size_t sl_off = 0, blocks[2];
+    block_sizes(r->plan, M, s->amp, blocks);
+    const size_t need = blocks[0] + blocks[1];
+    if (need > s->dev.size() || align256(n * 8) + tables_bytes(r->plan, &sl_off) > s->host.size())
         return sfail(QSIM_EBUSY, "request needs " + std::to_string(need) + " bytes, more than the budget");
     r->M = M;
     r->L = L;
     r->host_in = host_amps;
     r->t_submit = Clock::now();
-    cudaEventCreateWithFlags(&r->uploaded, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&r->finished, cudaEventDisableTiming);
+    cudaEventCreate(&r->uploaded);
+    cudaEventCreateWithFlags(&r->computed, cudaEventDisableTiming);
+    cudaEventCreate(&r->finished);
+    cudaEventCreate(&r->up0);
+    cudaEventCreate(&r->down0);
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     s->waiting.push_back(r);
@@ -485,7 +663,10 @@ int qsim_server_release(qsim_server *s, uint64_t id)
     if (it->second->state != Request::kDone) return sfail(QSIM_EBUSY, "request still running");
     s->host.release(it->second->host_off);
     cudaEventDestroy(it->second->uploaded);
+    cudaEventDestroy(it->second->computed);
     cudaEventDestroy(it->second->finished);
+    cudaEventDestroy(it->second->up0);
+    cudaEventDestroy(it->second->down0);
     s->all.erase(it);
     s->cv.notify_all();
     return QSIM_OK;
@@ -502,6 +683,59 @@ int qsim_server_wait_all(qsim_server *s, double timeout_s)
             !(s->waiting.empty() && s->active.empty()))
             return sfail(QSIM_ETIMEOUT, "requests still pending");
     }
+    return QSIM_OK;
+}
+
+int qsim_server_set_backfill(qsim_server *s, double max_head_wait_ms)
+{
+    if (!s) return sfail(QSIM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->max_head_wait_ms = max_head_wait_ms;
+    return QSIM_OK;
+}
+
+int qsim_server_set_paused(qsim_server *s, int paused)
+{
+    if (!s) return sfail(QSIM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+    s->cv.notify_all();
+    return QSIM_OK;
+}
+
+int qsim_server_set_tracing(qsim_server *s, int enable)
+{
+    if (!s) return sfail(QSIM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (enable && !s->tracing) {
+        s->trace.clear();
+        if (!s->t0_event && cudaEventCreate(&s->t0_event) != cudaSuccess)
+            return sfail(QSIM_ECUDA, "cudaEventCreate(trace origin)");
+        cudaEventRecord(s->t0_event, s->h2d);
+        cudaEventSynchronize(s->t0_event);
+        s->t0 = Clock::now();
+    }
+    s->tracing = enable != 0;
+    return QSIM_OK;
+}
+
+int qsim_server_get_trace(qsim_server *s, qsim_server_trace_record *out, size_t cap, size_t *n_out)
+{
+    if (!s || !n_out || (cap && !out)) return sfail(QSIM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t n = std::min(cap, s->trace.size());
+    if (n) std::memcpy(out, s->trace.data(), n * sizeof(qsim_server_trace_record));
+    s->trace.erase(s->trace.begin(), s->trace.begin() + (std::ptrdiff_t)n);
+    *n_out = n;
+    return QSIM_OK;
+}
+
+int qsim_server_set_copy_streams(qsim_server *s, int n)
+{
+    if (!s || (n != 1 && n != 2)) return sfail(QSIM_EINVAL, "copy streams must be 1 or 2");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->active.empty()) return sfail(QSIM_EBUSY, "requests are running");
+    s->copy_streams = n;
     return QSIM_OK;
 }
 
@@ -525,7 +759,10 @@ void qsim_server_destroy(qsim_server *s)
     cudaStreamSynchronize(s->d2h);
     for (auto &kv : s->all) {
         cudaEventDestroy(kv.second->uploaded);
+        cudaEventDestroy(kv.second->computed);
         cudaEventDestroy(kv.second->finished);
+        cudaEventDestroy(kv.second->up0);
+        cudaEventDestroy(kv.second->down0);
     }
     for (auto &sl : s->slots) {
         if (sl.d_passes) cudaFree(sl.d_passes);
@@ -533,11 +770,12 @@ void qsim_server_destroy(qsim_server *s)
         if (sl.h_passes) cudaFreeHost(sl.h_passes);
         if (sl.h_items) cudaFreeHost(sl.h_items);
         if (sl.d_counter) cudaFree(sl.d_counter);
+        if (sl.start) cudaEventDestroy(sl.start);
         if (sl.done) cudaEventDestroy(sl.done);
     }
     cudaFree(s->d_partials);
     cudaFree(s->d_norms);
-    cudaEventDestroy(s->probs_ready);
+    if (s->t0_event) cudaEventDestroy(s->t0_event);
     cudaFree(s->d_arena);
     cudaFreeHost(s->h_arena);
     cudaStreamDestroy(s->compute);

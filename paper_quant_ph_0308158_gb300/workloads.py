@@ -115,11 +115,14 @@ def random_state(M: int, dtype=np.complex128, seed: int = 0, out: np.ndarray | N
     return out
 
 
-def alternating_state(M: int, dtype=np.complex128) -> np.ndarray:
+def alternating_state(M: int, dtype=np.complex128, out: np.ndarray | None = None) -> np.ndarray:
     """(1, -1, 1, -1, ...)/sqrt(2^M): the input of the paper's Sec. 2b example
-    and of its Sec. 4 computational example."""
+    and of its Sec. 4 computational example (``out``: optional preallocated,
+    e.g. pinned, buffer)."""
     n = 1 << M
-    a = np.empty(n, dtype=dtype)
+    a = np.empty(n, dtype=dtype) if out is None else out
+    if a.shape != (n,) or a.dtype != np.dtype(dtype):
+        raise ValueError("out has the wrong shape or dtype")
     s = 1.0 / math.sqrt(n)
     a[0::2] = s
     a[1::2] = -s

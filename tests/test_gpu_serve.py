@@ -111,3 +111,62 @@ def test_admission_rejections():
         assert e.value.code == -1
         with pytest.raises(QsimError):
             srv.poll(12345)
+
+
+def _dev_bytes(M, amp=16):
+    """Device memory the server reserves for a one-pass request without plan
+    tables: the input state and a buffer for the probabilities."""
+    a = lambda x: (x + 255) // 256 * 256
+    return a((1 << M) * amp) + a((1 << M) * 8)
+
+
+@pytest.mark.parametrize("backfill_ms", [1e9, -1.0])
+def test_backfill_admission(backfill_ms):
+    """A request that does not fit while an earlier one runs is passed by
+    smaller requests that do (backfill), unless backfill is off; every result
+    still matches the oracle."""
+    big = [(16, W.random_state(16, np.complex128, 40 + i), W.cnot_circuit(16, 3000, 40 + i))
+           for i in range(2)]
+    small = [(8, W.random_state(8, np.complex128, 50 + i), W.mixed_circuit(8, 200, 50 + i))
+             for i in range(8)]
+    budget = _dev_bytes(16) * 3 // 2  # one large request at a time, the small ones beside it
+    with Server(budget, 64 << 20, np.complex128) as srv:
+        srv.set_backfill(backfill_ms)
+        srv.set_paused(True)
+        ids = [srv.submit(*r) for r in big + small]  # queue: big, big, small x 8
+        srv.set_paused(False)
+        srv.wait_all(300)
+        st = srv.stats()
+        if backfill_ms > 0:
+            assert st["backfilled"] >= 1
+        else:
+            assert st["backfilled"] == 0
+        assert st["completed"] == len(ids) and st["peak_in_use_bytes"] <= budget
+        for rid, (M, k1, steps) in zip(ids, big + small):
+            done, _, p = srv.poll(rid)
+            assert done
+            assert_probs_close(p, _expected(M, k1, steps))
+            srv.release(rid)
+        assert st["h2d_bytes"] == sum((1 << M) * 16 for M, _, _ in big + small)
+        assert st["d2h_bytes"] == sum((1 << M) * 8 for M, _, _ in big + small)
+        assert st["h2d_busy_ms"] > 0 and st["d2h_busy_ms"] > 0 and st["compute_busy_ms"] > 0
+
+
+def test_trace_records_each_request_in_order():
+    reqs = _requests(12, 9, 6, 14)
+    with Server(64 << 20, 64 << 20, np.complex128) as srv:
+        srv.set_tracing(True)
+        ids = [srv.submit(M, k1, st) for M, k1, st in reqs]
+        srv.wait_all(300)
+        tr = srv.trace()
+        assert sorted(tr["id"].tolist()) == sorted(ids)
+        for rec in tr:
+            assert rec["submit_ms"] <= rec["admit_ms"] <= rec["done_ms"]
+            assert 0 <= rec["upload_start_ms"] <= rec["upload_end_ms"]
+            assert rec["upload_end_ms"] <= rec["download_start_ms"] <= rec["download_end_ms"]
+            if rec["passes"]:
+                assert rec["upload_end_ms"] <= rec["compute_start_ms"] <= rec["compute_end_ms"]
+                assert rec["compute_end_ms"] <= rec["download_start_ms"]
+        assert len(srv.trace()) == 0  # moved out
+        for rid in ids:
+            srv.release(rid)
