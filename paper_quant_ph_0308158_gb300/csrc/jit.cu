@@ -122,15 +122,17 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
     const bool wide = M > 32;
     std::ostringstream s;
     s << "typedef unsigned int u32;\ntypedef unsigned long long u64;\n";
+    // random reads: read-only path with a 64-byte L2 fill (fewer DRAM bytes
+    // per 16-byte read than the default fill)
     if (amp == 16)
         s << "struct __align__(16) Amp { u32 a, b, c, d; };\n"
              "__device__ __forceinline__ Amp ldnc(const Amp* p) { Amp v; asm volatile("
-             "\"ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];\" : \"=r\"(v.a), \"=r\"(v.b), \"=r\"(v.c), "
+             "\"ld.global.nc.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4];\" : \"=r\"(v.a), \"=r\"(v.b), \"=r\"(v.c), "
              "\"=r\"(v.d) : \"l\"(p)); return v; }\n";
     else
         s << "struct __align__(8) Amp { u32 a, b; };\n"
              "__device__ __forceinline__ Amp ldnc(const Amp* p) { Amp v; asm volatile("
-             "\"ld.global.nc.v2.u32 {%0,%1}, [%2];\" : \"=r\"(v.a), \"=r\"(v.b) : \"l\"(p)); "
+             "\"ld.global.nc.L2::64B.v2.u32 {%0,%1}, [%2];\" : \"=r\"(v.a), \"=r\"(v.b) : \"l\"(p)); "
              "return v; }\n";
     // 32x32 bit transpose: five rounds of masked block swaps
     s << "__device__ __forceinline__ void tr32(u32 (&a)[32]) {\n"
@@ -143,7 +145,8 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
          "  }\n}\n";
     // FP64 probabilities of the gathered amplitudes (same functions as the
     // library's own kernels)
-    s << "#define QSIM_Q __device__ __forceinline__\n" << kProbMathSource << "\n";
+    s << "#define QSIM_Q __device__ __forceinline__\n#define QSIM_QN __device__ __noinline__\n"
+      << kProbMathSource << "\n";
     s << "extern \"C\" __global__ void __launch_bounds__(256) qsim_jit_gather("
          "const Amp* __restrict__ in, Amp* __restrict__ out, u64 n, double* __restrict__ probs) {\n"
          "  __shared__ u32 tabs[8 * 32 * 33];\n";

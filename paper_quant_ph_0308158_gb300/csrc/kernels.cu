@@ -39,9 +39,36 @@ template <> struct AmpOf<8> { using T = uint2; };
 template <> struct AmpOf<16> { using T = uint4; };
 
 // FP64 probability of one amplitude held as raw words (prob_math.cuh)
-QSIM_PROB_MATH(__device__ __forceinline__)
+QSIM_PROB_MATH(__device__ __forceinline__, __device__ __noinline__)
 __device__ __forceinline__ double amp_prob(const uint2 &v) { return qsim_prob_bits(v.x, v.y); }
 __device__ __forceinline__ double amp_prob(const uint4 &v) { return qsim_prob_bits(v.x, v.y, v.z, v.w); }
+
+// One amplitude at a data-dependent row (the gather's read).  FILL64: the
+// read-only path with a 64-byte L2 fill instead of the default larger one,
+// which cuts the DRAM bytes fetched per random 16-byte read of a large state;
+// otherwise the plain read-only load (better when the state sits in L2, as
+// the small states of a batch do).
+__device__ __forceinline__ uint2 ld_row64(const uint2 *p)
+{
+    uint2 v;
+    asm("ld.global.nc.L2::64B.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_row64(const uint4 *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+template <bool FILL64, typename A>
+__device__ __forceinline__ A ld_row(const A *p)
+{
+    if (FILL64) return ld_row64(p);
+    return __ldg(p);
+}
 
 // Insert a zero bit at position pos of x (bits >= pos move up by one).
 __device__ __forceinline__ uint64_t insert_zero(uint64_t x, uint32_t pos)
@@ -418,7 +445,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 
 // Affine gather of outputs [o0, o1): x(i) = b ^ XOR over index bytes of
 // per-byte tables (already in shared memory).
-template <int B, bool WIDE, typename I>
+template <int B, bool WIDE, typename I, bool FILL64>
 __device__ __forceinline__ void affine_range(const char *__restrict__ in, char *__restrict__ out,
                                              uint64_t o0, uint64_t o1, uint64_t step,
                                              const I *tab, uint32_t nbytes, uint64_t bvec,
@@ -437,7 +464,7 @@ __device__ __forceinline__ void affine_range(const char *__restrict__ in, char *
             if (i < o1) {
                 I x = (I)bvec;
                 for (uint32_t b = 0; b < nbytes; ++b) x ^= tab[b * 256 + ((i >> (8 * b)) & 255u)];
-                v[u] = __ldg(&src[x]);
+                v[u] = ld_row<FILL64>(&src[x]);
             }
         }
 #pragma unroll
@@ -460,7 +487,7 @@ __global__ void __launch_bounds__(kThreads) gather_affine_kernel(const char *__r
     __shared__ I tab[5 * 256];
     for (uint32_t i = threadIdx.x; i < nbytes * 256; i += kThreads) tab[i] = (I)tables[i];
     __syncthreads();
-    affine_range<B, WIDE, I>(in, out, (uint64_t)blockIdx.x * kThreads + threadIdx.x, n,
+    affine_range<B, WIDE, I, true>(in, out, (uint64_t)blockIdx.x * kThreads + threadIdx.x, n,
                              (uint64_t)gridDim.x * kThreads, tab, nbytes, bvec, probs);
 }
 
@@ -518,7 +545,7 @@ __host__ __device__ constexpr size_t sliced_smem_for(uint32_t M)
 // Every thread of the CTA must call it (it synchronises the CTA).  With MAP
 // the source rows x(i) themselves are written to out (64-bit integers, the
 // row array of the product, Sec. 2h) instead of gathering amplitudes.
-template <int B, bool WIDE, bool MAP = false>
+template <int B, bool WIDE, bool MAP = false, bool FILL64 = true>
 __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out, uint32_t M,
                              uint64_t n, const SlicedStep *__restrict__ steps, uint32_t nsteps,
                              uint64_t cbase, unsigned char *smem, double *__restrict__ probs)
@@ -612,7 +639,7 @@ __device__ void sliced_chunk(const char *__restrict__ in, char *__restrict__ out
                 if (MAP) {
                     if (o[u] < n) reinterpret_cast<uint64_t *>(out)[o[u]] = x;
                 } else if (o[u] < n) {
-                    v[u] = __ldg(&src[x]);
+                    v[u] = ld_row<FILL64>(&src[x]);
                 }
             }
             if (!MAP) {
@@ -707,11 +734,12 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__rest
                 __syncthreads();
                 if (threadIdx.x == 0) s_tables = (int32_t)item.pass;
             }
-            affine_range<B, WIDE, I>(P.in, P.out, item.start + threadIdx.x, o1, kThreads, tab,
+            affine_range<B, WIDE, I, false>(P.in, P.out, item.start + threadIdx.x, o1, kThreads, tab,
                                      P.nbytes, P.bvec, P.probs);
         } else if (P.kind == 4) {
             if (threadIdx.x == 0) s_tables = -1;
-            sliced_chunk<B, WIDE>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem, P.probs);
+            sliced_chunk<B, WIDE, false, false>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem,
+                                                P.probs);
         } else {
             sweep_range<B>(P.out, P.sweep, item.start + threadIdx.x, o1, kThreads);
         }

@@ -1,11 +1,12 @@
 // FP64 basis-state probability |k(i)|^2 of one amplitude.
 //
 // One definition serves both the kernels compiled with the library and the
-// circuit-specialised kernels generated at run time: QSIM_PROB_MATH(Q)
-// expands to the functions with the qualifiers Q, and kProbMathSource (below)
-// is the same token sequence as a string in which Q stays the identifier
-// QSIM_Q, for the generated source to define.  The body uses no macro, so
-// the string is exactly what the compiled library runs.
+// circuit-specialised kernels generated at run time: QSIM_PROB_MATH(Q, QN)
+// expands to the functions with the qualifiers Q (QN: the out-of-line
+// special-value path), and kProbMathSource (below) is the same token sequence
+// as a string in which they stay the identifiers QSIM_Q and QSIM_QN, for the
+// generated source to define.  The body uses no macro, so the string is
+// exactly what the compiled library runs.
 //
 // complex64: a float's significand s has at most 24 bits, so s^2 < 2^48 fits
 // a double's 53 bits and re^2, im^2 are exact doubles.  They are built in
@@ -16,16 +17,28 @@
 // to +0, infinity to infinity, NaN to a quiet NaN.  This keeps conversions
 // and multiplies off the FP64 pipe (its issue rate, not HBM, bounds an FP64
 // evaluation on GB300): the one FP64 instruction is the sum, whose rounding
-// is the only one, so the result equals squaring and adding in FP64.
+// is the only one, so the result equals squaring and adding in FP64.  Normal
+// numbers and zeros take a short inlined path (the significand square is
+// normalised by a shift of (P << 6) >> (P >> 47)); the rest an out-of-line
+// general one.
 //
 // complex128: im^2 rounded, then one fused multiply-add -- within one unit in
 // the last place of two separately rounded products.
 #pragma once
 
-#define QSIM_PROB_MATH(Q)                                                                   \
-    Q unsigned long long qsim_square_bits(float x)                                          \
+#define QSIM_PROB_MATH(Q, QN)                                                               \
+    Q unsigned long long qsim_square_bits_fast(unsigned int u)                              \
     {                                                                                       \
-        const unsigned int u = __float_as_uint(x);                                          \
+        const unsigned int e = (u >> 23) & 0xFFu;                                           \
+        const unsigned int s = (u & 0x7FFFFFu) | 0x800000u;                                 \
+        const unsigned long long P = (unsigned long long)s * s;                             \
+        const unsigned int top = (unsigned int)(P >> 47);                                   \
+        const unsigned long long S = (P << 6) >> top;                                       \
+        const unsigned long long bits = ((unsigned long long)(2u * e + 768u + top) << 52) + S; \
+        return (u << 1) ? bits : 0ull;                                                      \
+    }                                                                                       \
+    QN unsigned long long qsim_square_bits(unsigned int u)                                  \
+    {                                                                                       \
         const unsigned int e = (u >> 23) & 0xFFu;                                           \
         const unsigned int m = u & 0x7FFFFFu;                                               \
         const unsigned long long s = (unsigned long long)(e ? (m | 0x800000u) : m);         \
@@ -37,10 +50,18 @@
         if (e == 0xFFu) bits = m ? 0x7FF8000000000000ull : 0x7FF0000000000000ull;           \
         return bits;                                                                        \
     }                                                                                       \
+    Q bool qsim_square_fast_ok(unsigned int u)                                              \
+    {                                                                                       \
+        return (((u >> 23) & 0xFFu) - 1u) < 254u || (u << 1) == 0u;                         \
+    }                                                                                       \
     Q double qsim_prob_c64(float re, float im)                                              \
     {                                                                                       \
-        return __dadd_rn(__longlong_as_double((long long)qsim_square_bits(re)),             \
-                         __longlong_as_double((long long)qsim_square_bits(im)));            \
+        const unsigned int a = __float_as_uint(re), b = __float_as_uint(im);                \
+        if (qsim_square_fast_ok(a) && qsim_square_fast_ok(b))                               \
+            return __dadd_rn(__longlong_as_double((long long)qsim_square_bits_fast(a)),     \
+                             __longlong_as_double((long long)qsim_square_bits_fast(b)));    \
+        return __dadd_rn(__longlong_as_double((long long)qsim_square_bits(a)),              \
+                         __longlong_as_double((long long)qsim_square_bits(b)));             \
     }                                                                                       \
     Q double qsim_prob_c128(double re, double im) { return __fma_rn(re, re, __dmul_rn(im, im)); } \
     Q double qsim_prob_bits(unsigned int a, unsigned int b)                                 \
@@ -55,5 +76,6 @@
 #define QSIM_STRINGIFY_(...) #__VA_ARGS__
 #define QSIM_STRINGIFY(...) QSIM_STRINGIFY_(__VA_ARGS__)
 
-// The functions' source with qualifiers QSIM_Q.
-inline constexpr char kProbMathSource[] = QSIM_STRINGIFY(QSIM_PROB_MATH(QSIM_Q));
+// The functions' source with qualifiers QSIM_Q (inlined) and QSIM_QN (the
+// out-of-line path for subnormals, infinities and NaNs).
+inline constexpr char kProbMathSource[] = QSIM_STRINGIFY(QSIM_PROB_MATH(QSIM_Q, QSIM_QN));

@@ -190,13 +190,28 @@ def test_complex64_probabilities_bit_identical_including_special_values():
     parts *= np.exp2(rng.integers(-140, 120, size=parts.size)).astype(np.float32)
     parts[rng.integers(0, parts.size, size=4096)] = rng.choice(special, size=4096)
     k1 = parts.view(np.complex64)
-    want = oracle.probabilities(k1)
+
+    def same(got, want):
+        np.testing.assert_array_equal(got.view(np.uint64)[~np.isnan(want)],
+                                      want.view(np.uint64)[~np.isnan(want)])
+        assert np.array_equal(np.isnan(got), np.isnan(want))
+
     with Simulator(M, np.complex64) as sim:
         sim.load_state(k1)
-        got = sim.probabilities()
-    np.testing.assert_array_equal(got.view(np.uint64)[~np.isnan(want)],
-                                  want.view(np.uint64)[~np.isnan(want)])
-    assert np.array_equal(np.isnan(got), np.isnan(want))
+        same(sim.probabilities(), oracle.probabilities(k1))
+    # the same arithmetic where a tile or compiled-gather pass writes them
+    import torch
+    steps = W.random_circuit(M, 64, 12, max_controls=3)
+    want = oracle.probabilities(oracle.apply_circuit(M, k1, steps).astype(np.complex64))
+    for strategy, jit in (("tile", False), ("gather", True), ("gather", False)):
+        out = torch.empty(1 << M, dtype=torch.float64, device="cuda")
+        with Simulator(M, np.complex64) as sim:
+            sim.set_strategy(strategy)
+            sim.set_jit(jit)
+            sim.load_state(k1)
+            sim.apply_probabilities(steps, out.data_ptr())
+            sim.synchronize()
+        same(out.cpu().numpy(), want)
 
 
 # ----------------------------------------------------------------------------
