@@ -313,6 +313,12 @@ def run_ours(args, rank, ws, local):
         sim.set_jit(True)
     probs = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune:  # measured plan choice, before warm-up (not timed, like compilation)
+        load_input()
+        t0 = time.perf_counter()
+        cands = sim.autotune(steps, reps=1)
+        tuned = {"seconds": time.perf_counter() - t0, "chosen": cands[0], "candidates": cands}
 
     def step():
         if args.separate_probs:
@@ -466,6 +472,7 @@ def run_ours(args, rank, ws, local):
                        "probabilities": "separate pass" if args.separate_probs
                        else "written by the last pass",
                        "jit": bool(jit_ms is not None),
+                       "autotune": tuned,
                        "jit_compile_ms": jit_ms,
                        "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in by_kind.items()}},
             "roofline": roofline,
@@ -628,6 +635,67 @@ def serve_plain_baseline(specs, pool):
             "how": "first requests of the same stream, one at a time, closed loop"}
 
 
+def run_parity_scan(args, rank, ws, local):
+    """Sec. 4 computational example at every M of a range: the parity program
+    on the alternating input (generated on the device from its qubits, App. 1),
+    probabilities included, timed per M.  The paper reports its run time
+    growing about 3.4x per added qubit at M = 30-31 on modi4 (Sec. 4)."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Simulator, build
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    build.build()
+    torch.cuda.set_device(local)
+    lo, hi = args.scan_m_min, args.scan_m_max
+    rows = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for M in range(lo, hi + 1):
+        cfg = W.config_parity(M)
+        steps = cfg["steps"]
+        sim = Simulator(M, np.complex64, scratch=False)
+        sim.set_strategy("inplace")
+        sim.set_canonicalize(False)
+        probs = torch.empty(1 << M, dtype=torch.float64, device="cuda")
+        sim.load_product_state(cfg["qubits"])
+        for _ in range(args.warmup):
+            sim.apply_probabilities(steps, probs.data_ptr())
+        sim.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.apply_probabilities(steps, probs.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rows.append({"M": M, "L": len(steps), "ms": ms,
+                     "amp_steps_per_s": (1 << M) * len(steps) / (ms * 1e-3),
+                     "gb_per_s": (1 << M) * (8 + 8 + 8) / (ms * 1e-3) / 1e9})
+        sim.close()
+        del probs
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    growth = [rows[i + 1]["ms"] / rows[i]["ms"] for i in range(len(rows) - 1)]
+    top = rows[-1]
+    line = {
+        "metric": METRIC, "value": top["amp_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic (the Sec. 4 alternating input from its qubits)",
+        "config": {"workload": "parity_scan_M%d_%d" % (lo, hi),
+                   "step_includes": "one in-place tile pass + FP64 probabilities",
+                   "per_M": rows,
+                   "time_growth_per_qubit": growth,
+                   "time_growth_per_qubit_top4_mean": float(np.mean(growth[-4:])) if growth else None,
+                   "paper_growth_per_qubit_modi4": 3.4},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": len(rows) *
+        (args.steps + args.warmup), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args, rank, ws, local):
     """Serving: a Poisson stream of simulation requests through qsim_server
     (continuous batching under an HBM budget), FP64 probabilities out.
@@ -740,7 +808,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
-                             "batch_cnot", "batch_mixed", "serve"])
+                             "batch_cnot", "batch_mixed", "serve", "parity_scan"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
     ap.add_argument("--low-bits", type=int, default=0, help="contiguous low tile bits l (0: default)")
@@ -759,6 +827,10 @@ def main():
                     help="write a per-request timeline (CSV) of the serving run to this path")
     ap.add_argument("--serve-plain-requests", type=int, default=400,
                     help="requests timed one at a time for the plain comparison (0: skip)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time candidate plans first and keep the fastest (qsim_autotune)")
+    ap.add_argument("--scan-m-min", type=int, default=16)
+    ap.add_argument("--scan-m-max", type=int, default=33)
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
     ap.add_argument("--ref-steps-per-step", type=int, default=2,
                     help="oracle steps per timed reference step")
@@ -780,6 +852,8 @@ def main():
         rc = run_batch(args, rank, ws, local)
     elif args.workload == "serve":
         rc = run_serve(args, rank, ws, local) if rank == 0 else 0
+    elif args.workload == "parity_scan":
+        rc = run_parity_scan(args, rank, ws, local) if rank == 0 else 0
     else:
         rc = run_ours(args, rank, ws, local)
     if ws > 1:

@@ -166,6 +166,35 @@ int qsim_apply_circuit(qsim_ctx *ctx, const qsim_step *steps, size_t L);
 int qsim_apply_circuit_probabilities(qsim_ctx *ctx, const qsim_step *steps, size_t L,
                                      double *d_probs);
 
+/* One measured candidate plan of qsim_autotune. */
+typedef struct qsim_tune_result {
+    int strategy;       /* QSIM_STRATEGY_* */
+    int tile_bits;      /* tile width k for QSIM_STRATEGY_TILE (0: default)     */
+    int low_bits;       /* contiguous low tile bits l (0: default)              */
+    int jit;            /* compiled gather kernels allowed                      */
+    double ms;          /* fastest forward application over the repetitions;
+                           negative: the planner rejected the candidate         */
+    uint64_t passes;    /* passes of the plan                                   */
+} qsim_tune_result;
+
+/* Measure candidate plans for this circuit on the context's own state and
+ * keep the fastest (the strategy choice and tile shape of Sec. 2i's
+ * segmentation, picked by timing instead of the cost model).  Candidates:
+ * the cost model's choice (also restricted to in-place passes), the gathers
+ * with and without compiled kernels
+ * (when a second buffer is allowed), in-place tile passes for tile widths k
+ * of the default and the two below it and run lengths l = 3..6, and per-step
+ * sweeps when L <= 64.  Each candidate applies the circuit and then the
+ * reversed circuit (every step is its own inverse), reps + 1 times, timing
+ * the forward applications with CUDA events, so the state is unchanged at
+ * the end, bit for bit.  Synchronous.  out (cap entries, may be NULL with
+ * cap 0) receives the candidates fastest first; *n_out (may be NULL) their
+ * count.  Afterwards the context's strategy, tile shape and compiled-kernel
+ * switch are those of the fastest.  QSIM_EINVAL for an invalid circuit or
+ * reps outside 1..100; profiling records are not touched. */
+int qsim_autotune(qsim_ctx *ctx, const qsim_step *steps, size_t L, int reps, qsim_tune_result *out,
+                  size_t cap, size_t *n_out);
+
 /* The row array of the circuit's product (Sec. 2h) -- the information about
  * the unitary matrix that the paper's conclusions propose to keep for design
  * automation: d_rows[i] = x(i) with k2(i) = k1(x(i)) for k2 = U_L ... U_1 k1,

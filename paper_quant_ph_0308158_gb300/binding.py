@@ -42,7 +42,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 EXPORTS = (
     "qsim_create", "qsim_create_with_buffers", "qsim_destroy", "qsim_load_state",
     "qsim_read_state", "qsim_state_device", "qsim_apply_circuit",
-    "qsim_apply_circuit_probabilities", "qsim_set_strategy",
+    "qsim_apply_circuit_probabilities", "qsim_autotune", "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
@@ -100,6 +100,11 @@ class ServerStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int), ("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int),
+                ("jit", ctypes.c_int), ("ms", ctypes.c_double), ("passes", ctypes.c_uint64)]
+
+
 class ServerTraceRecord(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("M", ctypes.c_uint32), ("passes", ctypes.c_uint32),
                 ("L", ctypes.c_uint64), ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
@@ -138,6 +143,7 @@ def load() -> ctypes.CDLL:
             "qsim_state_device": ([p], p),
             "qsim_apply_circuit": ([p, p, sz], i),
             "qsim_apply_circuit_probabilities": ([p, p, sz, p], i),
+            "qsim_autotune": ([p, p, sz, i, p, sz, ctypes.POINTER(sz)], i),
             "qsim_set_strategy": ([p, i, i, i], i),
             "qsim_set_canonicalize": ([p, i], i),
             "qsim_set_profiling": ([p, i], i),
@@ -354,6 +360,19 @@ class Simulator:
         s = as_steps(steps)
         _check(self._lib.qsim_apply_circuit_probabilities(self._ctx, _ptr(s), len(s),
                                                           ctypes.c_void_p(out_ptr)))
+
+    def autotune(self, steps, reps: int = 2) -> list:
+        """Time candidate plans on this context's state (left unchanged) and keep
+        the fastest; returns the candidates fastest first as dicts."""
+        s = as_steps(steps)
+        buf = (TuneResult * 64)()
+        n = ctypes.c_size_t(0)
+        _check(self._lib.qsim_autotune(self._ctx, _ptr(s), len(s), int(reps), buf, 64,
+                                       ctypes.byref(n)))
+        names = {v: k for k, v in STRATEGY.items()}
+        return [{"strategy": names[r.strategy], "tile_bits": r.tile_bits, "low_bits": r.low_bits,
+                 "jit": bool(r.jit), "ms": r.ms, "passes": int(r.passes)}
+                for r in buf[:min(n.value, 64)]]
 
     def set_profiling(self, enable: bool):
         _check(self._lib.qsim_set_profiling(self._ctx, int(bool(enable))))

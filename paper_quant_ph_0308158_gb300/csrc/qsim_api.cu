@@ -534,6 +534,99 @@ int qsim_apply_circuit_probabilities(qsim_ctx *c, const qsim_step *steps, size_t
     return apply_impl(c, steps, L, d_probs);
 }
 
+int qsim_autotune(qsim_ctx *c, const qsim_step *steps, size_t L, int reps, qsim_tune_result *out,
+                  size_t cap, size_t *n_out)
+{
+    if (!c || (L && !steps)) return fail(QSIM_EINVAL, "NULL argument");
+    if (reps < 1 || reps > 100) return fail(QSIM_EINVAL, "reps must be in 1..100");
+    if (cap && !out) return fail(QSIM_EINVAL, "out is NULL");
+    std::string msg;
+    int rc = validate_steps(c->M, steps, L, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    rc = check_device(c);
+    if (rc != QSIM_OK) return rc;
+    // candidate plans: the cost model's choice, the gathers (when a second
+    // buffer is allowed), in-place tile passes over a range of tile widths k
+    // and run lengths l, and per-step sweeps for short circuits
+    std::vector<qsim_tune_result> cand;
+    auto add = [&](int strategy, int k, int l, int jit) {
+        qsim_tune_result r{};
+        r.strategy = strategy;
+        r.tile_bits = k;
+        r.low_bits = l;
+        r.jit = jit;
+        r.ms = -1.0;
+        cand.push_back(r);
+    };
+    add(QSIM_STRATEGY_AUTO, 0, 0, c->opts.jit ? 1 : 0);
+    add(QSIM_STRATEGY_INPLACE, 0, 0, 0);
+    if (c->opts.scratch_available) {
+        add(QSIM_STRATEGY_GATHER, 0, 0, 0);
+        if (c->M >= 10) add(QSIM_STRATEGY_GATHER, 0, 0, 1);
+    }
+    const int kdef = c->amp == 16 ? 13 : 14;
+    for (int k = kdef; k >= kdef - 2; --k) {
+        if (k > (int)c->M || k < 4) continue;
+        for (int l = 3; l <= 6 && l < k; ++l) add(QSIM_STRATEGY_TILE, k, l, 0);
+    }
+    if (L <= 64) add(QSIM_STRATEGY_SWEEP, 0, 0, 0);
+
+    const PlanOptions saved = c->opts;
+    const bool saved_prof = c->profiling;
+    c->profiling = false;
+    std::vector<qsim_step> rev(steps, steps + L);
+    std::reverse(rev.begin(), rev.end());  // each step is its own inverse (Sec. 2a)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QSIM_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    QSIM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    int err = QSIM_OK;
+    for (auto &cd : cand) {
+        c->opts = saved;
+        c->opts.strategy = cd.strategy;
+        c->opts.tile_bits = cd.tile_bits;
+        c->opts.low_bits = cd.low_bits;
+        c->opts.jit = cd.jit != 0;
+        // forward then backward leaves the state as it was, bit for bit; the
+        // first pair compiles and warms up, then the forward passes are timed
+        if (apply_impl(c, steps, L, nullptr) != QSIM_OK || apply_impl(c, rev.data(), L, nullptr) != QSIM_OK) {
+            err = check_device(c);
+            if (err != QSIM_OK) break;
+            continue;  // the planner rejects this candidate (e.g. a tile wider than allowed)
+        }
+        cd.passes = c->stats.passes;
+        double best = 1e300;
+        for (int r = 0; r < reps && err == QSIM_OK; ++r) {
+            cudaEventRecord(e0, c->stream);
+            if (apply_impl(c, steps, L, nullptr) != QSIM_OK) err = QSIM_ECUDA;
+            cudaEventRecord(e1, c->stream);
+            if (err == QSIM_OK && apply_impl(c, rev.data(), L, nullptr) != QSIM_OK) err = QSIM_ECUDA;
+            if (err == QSIM_OK) err = check_device(c);
+            float ms = 0.f;
+            if (err == QSIM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, (double)ms);
+        }
+        if (err != QSIM_OK) break;
+        cd.ms = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->profiling = saved_prof;
+    c->opts = saved;
+    if (err != QSIM_OK) return err;
+    std::stable_sort(cand.begin(), cand.end(), [](const qsim_tune_result &a, const qsim_tune_result &b) {
+        if ((a.ms < 0) != (b.ms < 0)) return b.ms < 0;
+        return a.ms < b.ms;
+    });
+    if (cand.empty() || cand[0].ms < 0) return fail(QSIM_EINVAL, "no candidate plan ran");
+    // the context keeps the fastest plan
+    c->opts.strategy = cand[0].strategy;
+    c->opts.tile_bits = cand[0].tile_bits;
+    c->opts.low_bits = cand[0].low_bits;
+    c->opts.jit = cand[0].jit != 0;
+    if (n_out) *n_out = cand.size();
+    for (size_t i = 0; i < cand.size() && i < cap; ++i) out[i] = cand[i];
+    return QSIM_OK;
+}
+
 int qsim_set_profiling(qsim_ctx *c, int enable)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");

@@ -526,3 +526,28 @@ def test_async_load_and_probabilities_on_two_contexts():
         b.close()
     for i in range(4):
         assert_probs_close(outs[i], want[i])
+
+
+# ----------------------------------------------------------------------------
+# autotuning
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype,M,L,scratch", [(np.complex128, 18, 300, True),
+                                               (np.complex64, 20, 200, False),
+                                               (np.complex128, 12, 40, True)])
+def test_autotune_keeps_the_state_and_picks_a_working_plan(dtype, M, L, scratch):
+    steps = W.mixed_circuit(M, L, seed=M)
+    k1 = W.random_state(M, dtype, M)
+    want = oracle.apply_circuit(M, k1, steps).astype(dtype)
+    with Simulator(M, dtype, scratch=scratch) as sim:
+        sim.load_state(k1)
+        res = sim.autotune(steps, reps=1)
+        np.testing.assert_array_equal(sim.read_state(), k1)  # forward + reverse = identity
+        ran = [r for r in res if r["ms"] >= 0]
+        assert ran and ran == sorted(ran, key=lambda r: r["ms"])
+        assert any(r["strategy"] == "tile" for r in ran)
+        assert scratch == any(r["strategy"] == "gather" for r in res)
+        sim.apply(steps)  # with the plan the tuner kept
+        np.testing.assert_array_equal(sim.read_state(), want)
+        with pytest.raises(QsimError):
+            sim.autotune(steps, reps=0)
