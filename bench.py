@@ -406,8 +406,7 @@ def run_ours(args, rank, ws, local):
                 streams[c].wait_event(loaded[1 - c])
             sm.load_state_async(h_in)
             loaded[c].record(streams[c])
-            sm.apply(steps)
-            sm.probabilities_async(outs[c].numpy())
+            sm.apply_probabilities_async(steps, outs[c].numpy())
 
         for i in range(2):  # warm both contexts
             e2e_step(i)

@@ -262,11 +262,22 @@ int qsim_synchronize(qsim_ctx *ctx);
  * device.  Synchronous. */
 int qsim_probabilities(qsim_ctx *ctx, double *host_probs, size_t n, double *norm_out);
 
-/* As qsim_probabilities without the norm, queued without waiting: chunks of
- * probabilities are computed on the context's stream and copied to
- * host_probs (2^M doubles, valid until the next qsim_synchronize) on a second
- * stream of the context.  qsim_synchronize waits for both. */
+/* As qsim_probabilities without the norm, queued without waiting: the
+ * probabilities are computed on the context's stream into a device buffer of
+ * the context (2^M doubles, allocated on first use; if that allocation fails,
+ * in chunks through two small buffers) and copied to host_probs (2^M
+ * doubles; must stay valid and unread until the next qsim_synchronize) on a
+ * second stream of the context.  qsim_synchronize waits for both. */
 int qsim_probabilities_async(qsim_ctx *ctx, double *host_probs, size_t n);
+
+/* qsim_apply_circuit, then the probabilities of the result to host_probs,
+ * queued without waiting: the circuit's last tile or gather pass writes them
+ * into the context's device buffer beside the amplitudes (see
+ * qsim_apply_circuit_probabilities), and one copy on the context's second
+ * stream brings them to host_probs (2^M doubles, valid after the next
+ * qsim_synchronize).  Errors as qsim_apply_circuit; QSIM_EINVAL if n != 2^M. */
+int qsim_apply_circuit_probabilities_async(qsim_ctx *ctx, const qsim_step *steps, size_t L,
+                                           double *host_probs, size_t n);
 
 /* As qsim_probabilities, into device memory d_probs (2^M doubles, 8-byte
  * aligned), queued on the context's stream.  norm_out (may be NULL) is a

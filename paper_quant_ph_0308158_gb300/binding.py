@@ -42,7 +42,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 EXPORTS = (
     "qsim_create", "qsim_create_with_buffers", "qsim_destroy", "qsim_load_state",
     "qsim_read_state", "qsim_state_device", "qsim_apply_circuit",
-    "qsim_apply_circuit_probabilities", "qsim_autotune", "qsim_set_strategy",
+    "qsim_apply_circuit_probabilities", "qsim_apply_circuit_probabilities_async", "qsim_autotune",
+    "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
@@ -143,6 +144,7 @@ def load() -> ctypes.CDLL:
             "qsim_state_device": ([p], p),
             "qsim_apply_circuit": ([p, p, sz], i),
             "qsim_apply_circuit_probabilities": ([p, p, sz, p], i),
+            "qsim_apply_circuit_probabilities_async": ([p, p, sz, p, sz], i),
             "qsim_autotune": ([p, p, sz, i, p, sz, ctypes.POINTER(sz)], i),
             "qsim_set_strategy": ([p, i, i, i], i),
             "qsim_set_canonicalize": ([p, i], i),
@@ -360,6 +362,15 @@ class Simulator:
         s = as_steps(steps)
         _check(self._lib.qsim_apply_circuit_probabilities(self._ctx, _ptr(s), len(s),
                                                           ctypes.c_void_p(out_ptr)))
+
+    def apply_probabilities_async(self, steps, out: np.ndarray):
+        """apply(steps), then FP64 probabilities into out (2^M float64, pinned
+        for speed), queued: valid after synchronize()."""
+        if out.dtype != np.float64 or out.shape != (self.n,) or not out.flags.c_contiguous:
+            raise QsimError(QSIM_EINVAL, "out must be a contiguous float64 array of 2^M entries")
+        s = as_steps(steps)
+        _check(self._lib.qsim_apply_circuit_probabilities_async(self._ctx, _ptr(s), len(s), _ptr(out),
+                                                                self.n))
 
     def autotune(self, steps, reps: int = 2) -> list:
         """Time candidate plans on this context's state (left unchanged) and keep

@@ -66,6 +66,10 @@ struct qsim_ctx {
     double *d_partials = nullptr;
     double *d_norms = nullptr;
     double *d_probs_chunk[2] = {nullptr, nullptr};  // double buffer for host probabilities
+    double *d_probs_full = nullptr;                   // whole-state buffer for asynchronous reads
+    cudaEvent_t full_copied = nullptr;                // its copy to the host is done
+    cudaEvent_t full_written = nullptr;               // the context's stream wrote it
+    bool full_pending = false;
     cudaStream_t copy_stream = nullptr;               // device-to-host copies of those chunks
     cudaEvent_t chunk_ready[2] = {nullptr, nullptr}, chunk_copied[2] = {nullptr, nullptr};
     PlanOptions opts;
@@ -105,6 +109,9 @@ void ctx_free(qsim_ctx *c)
     if (c->plan_ev) cudaEventDestroy(c->plan_ev);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_norms) cudaFree(c->d_norms);
+    if (c->d_probs_full) cudaFree(c->d_probs_full);
+    if (c->full_copied) cudaEventDestroy(c->full_copied);
+    if (c->full_written) cudaEventDestroy(c->full_written);
     for (int i = 0; i < 2; ++i) {
         if (c->d_probs_chunk[i]) cudaFree(c->d_probs_chunk[i]);
         if (c->chunk_ready[i]) cudaEventDestroy(c->chunk_ready[i]);
@@ -119,11 +126,14 @@ void ctx_free(qsim_ctx *c)
 // Read and clear the device error flag (waits for the stream).
 int check_device(qsim_ctx *c)
 {
-    QSIM_CUDA(cudaStreamSynchronize(c->stream), "kernel execution");
+    // ordered on the context's stream only: a copy on the legacy default
+    // stream would also wait for other work that runs there
     int flag = 0;
-    QSIM_CUDA(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    QSIM_CUDA(cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+              "read error flag");
+    QSIM_CUDA(cudaStreamSynchronize(c->stream), "kernel execution");
     if (flag) {
-        cudaMemset(c->d_err, 0, sizeof(int));
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
         return fail(QSIM_ETIMEOUT, "a bounded device wait gave up (error flag " +
                                        std::to_string(flag) + ")");
     }
@@ -674,7 +684,9 @@ int qsim_probabilities_device(qsim_ctx *c, double *d_probs, double *norm_out)
     if (norm_out) {
         int rc = check_device(c);
         if (rc != QSIM_OK) return rc;
-        QSIM_CUDA(cudaMemcpy(norm_out, c->d_norms, sizeof(double), cudaMemcpyDeviceToHost), "read norm");
+        QSIM_CUDA(cudaMemcpyAsync(norm_out, c->d_norms, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                  "read norm");
+        QSIM_CUDA(cudaStreamSynchronize(c->stream), "read norm");
     }
     return QSIM_OK;
 }
@@ -686,14 +698,77 @@ namespace {
 // stream); with norms, also the per-chunk norms.  Returns without waiting.
 int queue_host_probabilities(qsim_ctx *c, double *host_probs, bool norms, size_t *nchunks_out);
 
+// The whole-state probability buffer for asynchronous reads, allocated on
+// first use (nullptr and no error if it cannot be: callers fall back to the
+// chunked path).  The context's stream waits until the previous copy out of
+// it is done, so a new write never races the copy.
+double *full_probs_buffer(qsim_ctx *c)
+{
+    if (!c->d_probs_full) {
+        if (cudaMalloc(&c->d_probs_full, sizeof(double) * c->n) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_probs_full = nullptr;
+            return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&c->full_copied, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->full_written, cudaEventDisableTiming) != cudaSuccess)
+            return nullptr;
+    }
+    if (c->full_pending) {
+        if (cudaStreamWaitEvent(c->stream, c->full_copied, 0) != cudaSuccess) return nullptr;
+        c->full_pending = false;
+    }
+    return c->d_probs_full;
+}
+
+// After the context's stream has written the whole-state buffer: one copy of
+// it to the host on the copy stream.
+int copy_full_probabilities(qsim_ctx *c, double *host_probs)
+{
+    if (!c->copy_stream) {
+        QSIM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    }
+    QSIM_CUDA(cudaEventRecord(c->full_written, c->stream), "cudaEventRecord");
+    QSIM_CUDA(cudaStreamWaitEvent(c->copy_stream, c->full_written, 0), "cudaStreamWaitEvent");
+    QSIM_CUDA(cudaMemcpyAsync(host_probs, c->d_probs_full, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
+                              c->copy_stream),
+              "cudaMemcpy(probabilities)");
+    QSIM_CUDA(cudaEventRecord(c->full_copied, c->copy_stream), "cudaEventRecord");
+    c->full_pending = true;
+    return QSIM_OK;
+}
+
 }  // namespace
 
 int qsim_probabilities_async(qsim_ctx *c, double *host_probs, size_t n)
 {
     if (!c || !host_probs) return fail(QSIM_EINVAL, "NULL argument");
     if (n != c->n) return fail(QSIM_EINVAL, "n must equal 2^M");
+    if (double *d = full_probs_buffer(c)) {  // one kernel, one copy out
+        const int e = launch_probabilities(c->buf[c->cur], (int)c->amp, c->n, d, c->d_partials,
+                                           probabilities_partials_needed(), nullptr, c->stream);
+        if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "probabilities launch");
+        return copy_full_probabilities(c, host_probs);
+    }
     size_t nchunks = 0;
     return queue_host_probabilities(c, host_probs, false, &nchunks);
+}
+
+int qsim_apply_circuit_probabilities_async(qsim_ctx *c, const qsim_step *steps, size_t L,
+                                           double *host_probs, size_t n)
+{
+    if (!c || !host_probs) return fail(QSIM_EINVAL, "NULL argument");
+    if (n != c->n) return fail(QSIM_EINVAL, "n must equal 2^M");
+    double *d = full_probs_buffer(c);
+    if (!d) {  // no room for the whole buffer: apply, then chunked probabilities
+        int rc = qsim_apply_circuit(c, steps, L);
+        if (rc != QSIM_OK) return rc;
+        size_t nchunks = 0;
+        return queue_host_probabilities(c, host_probs, false, &nchunks);
+    }
+    int rc = apply_impl(c, steps, L, d);
+    if (rc != QSIM_OK) return rc;
+    return copy_full_probabilities(c, host_probs);
 }
 
 int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_out)
@@ -710,8 +785,10 @@ int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_o
     if (rc != QSIM_OK) return rc;
     if (norm_out) {
         std::vector<double> norms(nchunks);
-        QSIM_CUDA(cudaMemcpy(norms.data(), c->d_norms, sizeof(double) * nchunks, cudaMemcpyDeviceToHost),
+        QSIM_CUDA(cudaMemcpyAsync(norms.data(), c->d_norms, sizeof(double) * nchunks, cudaMemcpyDeviceToHost,
+                                  c->stream),
                   "read norms");
+        QSIM_CUDA(cudaStreamSynchronize(c->stream), "read norms");
         // pairwise over chunk sums
         while (norms.size() > 1) {
             std::vector<double> nx((norms.size() + 1) / 2);

@@ -513,19 +513,33 @@ def test_async_load_and_probabilities_on_two_contexts():
         with torch.cuda.stream(s2):
             b = Simulator(M, np.complex128)
         sims = (a, b)
-        outs = [np.zeros(1 << M) for _ in range(4)]
-        for i in range(4):
+        outs = [np.zeros(1 << M) for _ in range(8)]
+        for i in range(8):  # separate probability pass, then fused into the circuit's pass
             sm = sims[i & 1]
             if i >= 2:
                 sm.synchronize()
-            sm.load_state_async(states[i])
-            sm.apply(steps)
-            sm.probabilities_async(outs[i])
+            sm.load_state_async(states[i % 4])
+            if i < 4:
+                sm.apply(steps)
+                sm.probabilities_async(outs[i])
+            else:
+                sm.apply_probabilities_async(steps, outs[i])
         for sm in sims:
             sm.synchronize()
         b.close()
-    for i in range(4):
-        assert_probs_close(outs[i], want[i])
+    for i in range(8):
+        assert_probs_close(outs[i], want[i % 4])
+    # back-to-back asynchronous reads on one context reuse its buffer safely
+    with Simulator(M, np.complex128) as a:
+        r = [np.zeros(1 << M) for _ in range(3)]
+        a.load_state(states[0])
+        a.probabilities_async(r[0])
+        a.apply_probabilities_async(steps, r[1])
+        a.apply_probabilities_async(steps[::-1], r[2])
+        a.synchronize()
+    assert_probs_close(r[0], oracle.probabilities(states[0]))
+    assert_probs_close(r[1], want[0])
+    assert_probs_close(r[2], oracle.probabilities(states[0]))
 
 
 # ----------------------------------------------------------------------------
