@@ -42,6 +42,43 @@ def test_step_record_layout_matches_header():
     assert W.STEP_DTYPE.fields["ctrl_mask"][1] == 8
 
 
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every public struct of include/qsim.h has the size and field offsets
+    the ctypes binding assumes (compiled with the host C compiler)."""
+    import ctypes
+    import subprocess
+    from paper_quant_ph_0308158_gb300 import binding as B
+    structs = {"qsim_plan_stats": B.PlanStats, "qsim_batch_stats": B.BatchStats,
+               "qsim_server_stats": B.ServerStats, "qsim_server_trace_record": B.ServerTraceRecord,
+               "qsim_tune_result": B.TuneResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qsim.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    for f in W.STEP_DTYPE.names:
+        lines.append('printf("qsim_step %s %%zu\\n", offsetof(qsim_step, %s));' % (f, f))
+    lines.append('printf("qsim_step size %zu\\n", sizeof(qsim_step));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    assert got[("qsim_step", "size")] == W.STEP_DTYPE.itemsize
+    for f in W.STEP_DTYPE.names:
+        assert got[("qsim_step", f)] == W.STEP_DTYPE.fields[f][1], f
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 
 @pytest.mark.parametrize("strategy", ["auto", "sweep", "tile", "gather", "inplace"])
 @pytest.mark.parametrize("M,L,seed", [(6, 200, 1), (10, 400, 2), (13, 300, 3)])
