@@ -276,7 +276,7 @@ def run_ours(args, rank, ws, local):
     L = len(steps)
     n = 1 << M
     amp = dtype.itemsize
-    strategy = strategy_for(args.workload)
+    strategy = args.strategy or strategy_for(args.workload)
     tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
 
     # seeded state in pinned host memory (also the e2e input buffer), or the
@@ -303,11 +303,12 @@ def run_ours(args, rank, ws, local):
         else:
             sim.load_product_state(qubits)
 
-    sim = Simulator(M, dtype, scratch=(strategy != "inplace"))
+    scratch = strategy in ("auto", "gather")  # the other strategies work in place
+    sim = Simulator(M, dtype, scratch=scratch)
     sim.set_strategy(strategy, args.tile_bits, args.low_bits)
     sim.set_canonicalize(False)
     jit_ms = None
-    if args.jit and strategy != "inplace":
+    if args.jit and scratch:
         from paper_quant_ph_0308158_gb300 import jit_precompile
         jit_ms = jit_precompile(M, dtype, steps, canonicalize=False)
         sim.set_jit(True)
@@ -386,7 +387,7 @@ def run_ours(args, rank, ws, local):
         d2h = n * 8
         s2 = torch.cuda.Stream()
         with torch.cuda.stream(s2):
-            sim2 = Simulator(M, dtype, scratch=(strategy != "inplace"))
+            sim2 = Simulator(M, dtype, scratch=scratch)
         sim2.set_strategy(strategy, args.tile_bits, args.low_bits)
         sim2.set_canonicalize(False)
         if jit_ms is not None:
@@ -826,6 +827,8 @@ def main():
                     help="write a per-request timeline (CSV) of the serving run to this path")
     ap.add_argument("--serve-plain-requests", type=int, default=400,
                     help="requests timed one at a time for the plain comparison (0: skip)")
+    ap.add_argument("--strategy", default="", choices=["", "auto", "sweep", "tile", "gather", "inplace"],
+                    help="force a strategy (default: the workload's)")
     ap.add_argument("--autotune", action="store_true",
                     help="time candidate plans first and keep the fastest (qsim_autotune)")
     ap.add_argument("--scan-m-min", type=int, default=16)

@@ -136,7 +136,6 @@ struct Request {
 struct qsim_server {
     int dtype = 0;
     size_t amp = 0;
-    uint32_t max_M = 0;
     char *d_arena = nullptr;
     char *h_arena = nullptr;
     Arena dev, host;
