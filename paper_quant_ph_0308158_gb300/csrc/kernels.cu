@@ -237,7 +237,7 @@ __device__ __forceinline__ void consumer_sync()
 // producer finds the CTA's next tile with an active step, publishes its
 // base and active-step mask in the stage's metadata, and issues one bulk
 // copy per contiguous run of 2^l amplitudes; an empty tile marks the end.
-template <int B>
+template <int B, bool PROBS>
 __global__ void __launch_bounds__(kTileThreads + 32, 1)
     tile_kernel(TileKParams p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                     mask[w] = __ballot_sync(0xffffffffu, act);
                     any |= mask[w] != 0;
                 }
-                if (any || p.probs) break;  // a pass that writes probabilities visits every tile
+                if (any || PROBS) break;  // a pass that writes probabilities visits every tile
                 base = kNoTile;
             }
             bool same = have_last && base != kNoTile;
@@ -367,10 +367,10 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
         }
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
-        bool idle = true;  // no active step: only a pass writing probabilities sends such a tile
+        bool idle = PROBS;  // no active step: only a pass writing probabilities sends such a tile
 #pragma unroll
         for (int w = 0; w < kMaskWords; ++w) idle = idle && meta[s].mask[w] == 0u;
-        if (idle) {
+        if (PROBS && idle) {
             const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
             for (uint32_t j = tid; j < tile_amps; j += kTileThreads)
                 p.probs[base + depo[j >> p.l] + (j & lmask)] = amp_prob(buf[j]);
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                 if (j < tile_amps) {
                     const uint64_t g = base + depo[j >> p.l] + (j & lmask);
                     st[g] = v[e];
-                    if (p.probs) p.probs[g] = amp_prob(v[e]);
+                    if (PROBS) p.probs[g] = amp_prob(v[e]);
                 }
             }
         }
@@ -976,18 +976,17 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     const int grid = (int)(t.n_tiles < cap ? t.n_tiles : cap);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (amp_bytes == 8) {
-        e = cudaFuncSetAttribute(tile_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        tile_kernel<8><<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
-    } else {
-        e = cudaFuncSetAttribute(tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        tile_kernel<16><<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
-    }
-    return cudaGetLastError();
+    // the pass that writes probabilities is its own instantiation, so the
+    // other passes carry no per-amplitude test
+    auto run = [&](auto kernel) -> cudaError_t {
+        cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        kernel<<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
+        return cudaGetLastError();
+    };
+    if (amp_bytes == 8) e = d_probs ? run(tile_kernel<8, true>) : run(tile_kernel<8, false>);
+    else e = d_probs ? run(tile_kernel<16, true>) : run(tile_kernel<16, false>);
+    return e;
 }
 
 static size_t sliced_smem_bytes(uint32_t M) { return sliced_smem_for(M); }
