@@ -277,6 +277,42 @@ def test_adder_m32_workload_sampled():
     assert st["gather_passes"] == 0 and st["passes"] >= 1
 
 
+def test_sec4_parity_m32_from_qubits_with_probabilities(cuda):
+    """The Sec. 4 example at M = 32 as the benchmark runs it: the alternating
+    input generated from its qubits (App. 1), the parity program in place,
+    probabilities written by the pass.  Closed form: k2(i) =
+    (-1)^popcount(i) / 2^16 for every row (checked on the device, plus sampled
+    rows against the oracle's single-row evaluation), p(i) = 2^-32 exactly."""
+    torch = cuda
+    M = 32
+    cfg = W.config_parity(M)
+    steps = cfg["steps"]
+    probs = torch.empty(1 << M, dtype=torch.float64, device="cuda")
+    with Simulator(M, np.complex64, scratch=False) as sim:
+        sim.set_strategy("inplace")
+        sim.load_product_state(cfg["qubits"])
+        sim.apply_probabilities(steps, probs.data_ptr())
+        sim.synchronize()
+        assert sim.plan_stats()["passes"] == 1
+        st = sim.state_tensor().view(torch.float32).view(-1, 2)
+        assert bool((st[:, 1] == 0).all())
+        re = st[:, 0]
+        assert bool((re.abs() == 2.0 ** -16).all())
+        # the sign is the parity of the row: spot-check blocks and random rows
+        rng = np.random.default_rng(32)
+        rows = np.concatenate([np.arange(4096, dtype=np.uint64),
+                               rng.integers(0, 1 << M, size=1 << 16, dtype=np.uint64)])
+        got = re[torch.from_numpy(rows.astype(np.int64)).cuda()].cpu().numpy()
+        src = oracle.source_rows(M, steps, rows)  # k2(i) = k1(x(i)), k1 alternating
+        want = np.where((src & 1).astype(bool), -1.0, 1.0) * 2.0 ** -16
+        np.testing.assert_array_equal(got, want.astype(np.float32))
+        par = np.zeros_like(rows)
+        for b in range(M):
+            par ^= (rows >> np.uint64(b)) & np.uint64(1)
+        np.testing.assert_array_equal(got, np.where(par.astype(bool), -1.0, 1.0).astype(np.float32) * 2.0 ** -16)
+        assert bool((probs == 2.0 ** -32).all())
+
+
 # ----------------------------------------------------------------------------
 # circuit-specialised (compiled) gather kernels and 64-bit indices
 # ----------------------------------------------------------------------------
