@@ -295,6 +295,12 @@ int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *c
     return rc;
 }
 
+int jit_prepare(uint32_t M, int amp, const qsim_step *steps, size_t n, std::string *msg)
+{
+    JitEntry *e = nullptr;
+    return jit_get(M, amp, steps, n, true, &e, msg);
+}
+
 int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
                       size_t n, double *d_probs, void *stream, std::string *msg)
 {

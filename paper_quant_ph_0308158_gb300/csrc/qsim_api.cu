@@ -473,6 +473,14 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
         rc = ensure_scratch(c);
         if (rc != QSIM_OK) return rc;
     }
+    // compile every circuit-specialised kernel before the first launch, so a
+    // compile failure leaves the state untouched
+    for (const Pass &p : plan.passes) {
+        if (p.kind != kGather || !p.gather.jit) continue;
+        std::string jmsg;
+        rc = jit_prepare(c->M, (int)c->amp, plan.jit_steps.data() + p.gather.jit_off, p.gather.jit_n, &jmsg);
+        if (rc != QSIM_OK) return fail(rc, jmsg);
+    }
     // one contiguous table: tile steps | sliced steps | gather tables
     const size_t off_tile = 0;
     const size_t sz_tile = plan.tile_steps.size() * sizeof(TileStep);

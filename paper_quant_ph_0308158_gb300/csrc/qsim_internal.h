@@ -198,6 +198,8 @@ size_t tile_smem_bytes(int amp_bytes, int k);
 // Compiled gather (jit.cu).  Return QSIM_OK or a QSIM_* error with msg set.
 int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *compile_ms,
                 std::string *msg);
+// Compile and load a compiled gather ahead of its launch (cached).
+int jit_prepare(uint32_t M, int amp, const qsim_step *steps, size_t n, std::string *msg);
 int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
                       size_t n, double *d_probs, void *stream, std::string *msg);
 int num_sms();
