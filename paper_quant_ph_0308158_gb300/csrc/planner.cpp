@@ -369,6 +369,18 @@ void plan_tiles(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> 
                 if (++deferred > 96 || (def_targets | def_controls) == full_mask(M)) break;
             }
         }
+        if (seg.empty()) {
+            // the first pending step fits no tile (a geometry with no free
+            // high bit and a target above the low bits): it becomes a sweep
+            seg.push_back(order[first]);
+            seg_pos.push_back(first);
+            done[first] = 1;
+            plan->passes.push_back(make_sweep(M, steps[order[first]], o.amp_bytes));
+            plan->order.push_back(order[first]);
+            plan->pass_ends.push_back(plan->order.size());
+            while (first < n && done[first]) ++first;
+            continue;
+        }
         for (size_t j : seg_pos) done[j] = 1;
         if (seg.size() == 1 && sweep_singles) {
             plan->passes.push_back(make_sweep(M, steps[seg[0]], o.amp_bytes));

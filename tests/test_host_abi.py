@@ -123,6 +123,23 @@ def test_tile_passes_respect_the_tile_width():
     assert len(plan["pass_ends"]) <= naive
 
 
+def test_tile_geometry_without_high_bits_falls_back_to_sweeps():
+    """A forced tile width equal to the run length leaves no tile bit above
+    the low ones: steps with higher targets must become sweeps (the planner
+    once looped on them) and the plan must still be the circuit."""
+    M = 22
+    steps = W.random_circuit(M, 142, 291, max_controls=3)
+    r = plan_circuit(M, np.complex128, steps, strategy="tile", tile_bits=6, low_bits=6, scratch=False)
+    assert "sweep" in r["kinds"] and "tile" in r["kinds"]
+    order = r["order"]
+    assert sorted(order.tolist()) == list(range(len(steps)))
+    k1 = W.random_state(14, np.complex128, 1)
+    small = W.random_circuit(14, 80, 5, max_controls=3)
+    rs = plan_circuit(14, np.complex128, small, strategy="tile", tile_bits=6, low_bits=6, scratch=False)
+    np.testing.assert_array_equal(oracle.apply_circuit(14, k1, small[rs["order"]]),
+                                  oracle.apply_circuit(14, k1, small))
+
+
 def test_cnot_only_circuit_is_one_affine_gather_pass():
     steps = W.cnot_circuit(16, 64, 1)
     plan = plan_circuit(16, np.complex128, steps, "gather")
