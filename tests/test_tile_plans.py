@@ -1,9 +1,17 @@
-"""Host check of the tile planner's layouts and step encodings: compiles
-tests/native/tile_plan_check.cpp (which includes the planner's source) with
-the host compiler and runs it.  No GPU."""
+"""Host checks of the planner's pass encodings: compiles the programs in
+tests/native/ (which include the planner's source) with the host compiler
+and runs them.  No GPU.
+
+- tile_plan_check: tile layouts (tensor-map copies in bounds, aligned, moving
+  the amplitudes the local order names) and per-tile step encodings;
+- gather_plan_check: affine tables, bit-sliced descriptors, compiled step
+  lists and sweep pair enumeration, each evaluated on sampled rows against
+  the circuit's own steps."""
 import os
 import resource
 import subprocess
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -12,10 +20,11 @@ def _limit_memory():
     resource.setrlimit(resource.RLIMIT_AS, (4 << 30, 4 << 30))
 
 
-def test_tile_layouts_and_step_encodings(tmp_path):
-    exe = tmp_path / "tile_plan_check"
+@pytest.mark.parametrize("program", ["tile_plan_check", "gather_plan_check"])
+def test_planner_encodings(tmp_path, program):
+    exe = tmp_path / program
     subprocess.run(["g++", "-O2", "-std=c++17", "-o", str(exe),
-                    os.path.join(ROOT, "tests", "native", "tile_plan_check.cpp")], check=True)
+                    os.path.join(ROOT, "tests", "native", program + ".cpp")], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300,
                        preexec_fn=_limit_memory)
     assert r.returncode == 0, r.stdout + r.stderr
