@@ -10,6 +10,7 @@ rebuilt whenever a source or header is newer than it.
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -26,7 +27,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas"
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wextra", "-Wno-unused-parameter"]
 
 SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "jit.cu", "batch.cu", "server.cu", "planner.cpp"]
-HEADERS = [os.path.join(CSRC, "qsim_internal.h"), os.path.join(ROOT, "include", "qsim.h")]
+HEADERS = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+    os.path.join(ROOT, "include", "qsim.h")]
 
 
 def _nvcc() -> str:

@@ -33,6 +33,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "qsim_internal.h"
 
 using namespace qsim;
@@ -46,60 +47,6 @@ int sfail(int code, const std::string &msg)
     set_last_error(msg);
     return code;
 }
-
-// First-fit allocator over [0, size) with 256-byte granularity; coalesces on free.
-class Arena {
-  public:
-    void init(size_t size) { free_[0] = size; size_ = size; }
-    bool alloc(size_t bytes, size_t *off)
-    {
-        bytes = (bytes + 255) / 256 * 256;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += bytes;
-                peak_ = std::max(peak_, used_);
-                sizes_[*off] = bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off)
-    {
-        auto s = sizes_.find(off);
-        if (s == sizes_.end()) return;
-        size_t bytes = s->second;
-        sizes_.erase(s);
-        used_ -= bytes;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + bytes == next->first) {
-            bytes += next->second;
-            free_.erase(next);
-        }
-        auto nx = free_.lower_bound(off);
-        if (nx != free_.begin()) {
-            auto prev = std::prev(nx);
-            if (prev->first + prev->second == off) {
-                prev->second += bytes;
-                return;
-            }
-        }
-        free_[off] = bytes;
-    }
-    size_t used() const { return used_; }
-    size_t peak() const { return peak_; }
-    size_t size() const { return size_; }
-
-  private:
-    std::map<size_t, size_t> free_;   // offset -> length
-    std::map<size_t, size_t> sizes_;  // allocated offset -> length
-    size_t used_ = 0, peak_ = 0, size_ = 0;
-};
 
 struct Request {
     uint64_t id = 0;

@@ -6,7 +6,9 @@ and runs them.  No GPU.
   the amplitudes the local order names) and per-tile step encodings;
 - gather_plan_check: affine tables, bit-sliced descriptors, compiled step
   lists and sweep pair enumeration, each evaluated on sampled rows against
-  the circuit's own steps."""
+  the circuit's own steps;
+- arena_check: the serving budget's first-fit allocator (coverage, no
+  overlap, merged free blocks, counters)."""
 import os
 import resource
 import subprocess
@@ -20,7 +22,7 @@ def _limit_memory():
     resource.setrlimit(resource.RLIMIT_AS, (4 << 30, 4 << 30))
 
 
-@pytest.mark.parametrize("program", ["tile_plan_check", "gather_plan_check"])
+@pytest.mark.parametrize("program", ["tile_plan_check", "gather_plan_check", "arena_check"])
 def test_planner_encodings(tmp_path, program):
     exe = tmp_path / program
     subprocess.run(["g++", "-O2", "-std=c++17", "-o", str(exe),
