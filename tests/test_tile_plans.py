@@ -31,3 +31,28 @@ def test_planner_encodings(tmp_path, program):
                        preexec_fn=_limit_memory)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok:"), r.stdout
+
+
+def test_c_program_builds_against_the_abi(tmp_path):
+    """A plain C program compiles against include/qsim.h and links against
+    libqsim.so (it is run by the GPU test below)."""
+    from paper_quant_ph_0308158_gb300 import build
+    lib = build.build()
+    exe = tmp_path / "c_abi_usage"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), os.path.join(ROOT, "tests", "native", "c_abi_usage.c"),
+                    "-L", os.path.dirname(lib), "-lqsim", "-Wl,-rpath," + os.path.dirname(lib), "-lm"],
+                   check=True)
+    assert exe.exists()
+
+
+@pytest.mark.gpu
+def test_c_program_runs_the_figure2_circuit(tmp_path):
+    from paper_quant_ph_0308158_gb300 import build
+    lib = build.build()
+    exe = tmp_path / "c_abi_usage"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "native", "c_abi_usage.c"), "-L", os.path.dirname(lib),
+                    "-lqsim", "-Wl,-rpath," + os.path.dirname(lib), "-lm"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
