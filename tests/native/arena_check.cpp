@@ -1,5 +1,5 @@
 // Host check of the serving budget's first-fit allocator (built and run by
-// tests/test_tile_plans.py, no GPU): random allocation and release sequences
+// tests/test_native_checks.py, no GPU): random allocation and release sequences
 // against the invariants -- blocks are 256-byte multiples inside the arena,
 // allocated and free blocks never overlap and together cover it exactly,
 // adjacent free blocks are always merged, the used and peak counters agree,

@@ -1,5 +1,5 @@
 /* A plain C program against the C ABI (compiled and linked by
- * tests/test_tile_plans.py on the host; it runs only where a GPU is present).
+ * tests/test_native_checks.py on the host; it runs only where a GPU is present).
  * It applies a three-step wiring diagram -- the Figure 2 circuit of the
  * paper: NOT a(2); a(2) controls a(1); NOT a(2) -- to the Sec. 2b input
  * (1, -1, 1, -1)/2 and checks the state and probabilities, then checks an

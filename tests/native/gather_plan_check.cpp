@@ -1,5 +1,5 @@
 // Host check of the gather and sweep planning (built and run by
-// tests/test_tile_plans.py, no GPU).  It includes the planner's source and,
+// tests/test_native_checks.py, no GPU).  It includes the planner's source and,
 // for the plans of random circuits, evaluates every pass's encoding on
 // sampled rows the way its kernel does, against the circuit's own steps:
 //   - affine passes: x(i) = b ^ XOR over index bytes of the per-byte tables;

@@ -1,4 +1,4 @@
-// Host check of the tile planner (built and run by tests/test_tile_plans.py,
+// Host check of the tile planner (built and run by tests/test_native_checks.py,
 // no GPU).  It includes the planner's source and verifies, for random tile
 // geometries and for the plans of random circuits:
 //   1. the local bit order covers the tile's address bits exactly once, and
