@@ -1,7 +1,7 @@
 """Benchmark: amplitude-steps/s of a reversible wiring diagram on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mixed_m28|adder_m32|cnot_m16]
+                    [--workload adder_m32|mixed_m28|cnot_m16|...] [--also mixed_m28]
 
 One timed step = one pass of the whole hot path over the resident state:
 validate + plan the circuit, apply all of its steps and compute the FP64
@@ -11,10 +11,15 @@ beside the state; --separate-probs times qsim_apply_circuit followed by
 qsim_probabilities_device instead).  value = 2^M * L * K / (device time of
 K steps).
 
-Default workload: M=28 complex128 (4 GiB state, larger than L2), L=1000 steps
-of the NOT / CNOT / Toffoli / 3-5-control NOT mix, seeded synthetic state and
-circuit.  Adjacent-equal-step cancellation is switched off, so every one of
-the L steps is applied.
+Default workload: M=32 complex64 (32 GiB state, in place, larger than L2):
+the ripple-carry adder of two 15-bit registers with carry-in and carry-out,
+two additions per unit, unit repeated 8 times (1456 CNOT / Toffoli steps),
+lines placed on address bits by a seeded permutation; seeded synthetic
+state.  Adjacent-equal-step cancellation is switched off, so every one of the
+L steps is applied.  The same line also carries the M=28 complex128 workload
+of 1000 NOT / CNOT / Toffoli / 3-5-control NOT steps (key "also", resident
+timing only) and the batched-vs-plain comparison on 4096 circuits of both
+gate mixes (key "batch").
 
 Also reported on the same JSON line:
   e2e          the same metric through the C ABI with host buffers: each step
@@ -215,44 +220,83 @@ def ncu_traffic(kernel: str, wl: str):
 # reference arm / CPU baseline: the oracle
 # ----------------------------------------------------------------------------
 
-def oracle_sample_rate(cfg, n_steps: int, k1=None):
-    """Time the CPU oracle applying the first n_steps of the circuit to the full
-    state (single thread).  Returns (amp-steps/s, seconds)."""
-    import oracle
-    oracle.build()
+def _host_free_bytes() -> int:
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        return 0
+
+
+def oracle_state(cfg, k1=None):
+    """The workload's state in the oracle's FP64 complex storage (built before
+    any timing), or None when the host lacks the memory for it."""
     M = cfg["M"]
+    need = 16 << M
+    if k1 is None:
+        need += np.dtype(cfg["dtype"]).itemsize << M
+    if _host_free_bytes() and _host_free_bytes() < need + (4 << 30):
+        return None
     if k1 is None:
         k1 = W.random_state(M, cfg["dtype"], cfg["state_seed"])
-    steps = cfg["steps"][:n_steps]
+    return np.asarray(k1).astype(np.complex128)
+
+
+def oracle_steps_rate(M: int, k: np.ndarray, steps):
+    """Time the CPU oracle's step-by-step loop (single thread) applying steps
+    in place to the full FP64 state.  Returns (amp-steps/s, seconds)."""
+    import oracle
     t0 = time.perf_counter()
-    oracle.apply_circuit(M, k1, steps)
+    oracle.apply_circuit_inplace(M, k, steps)
     dt = time.perf_counter() - t0
-    return (1 << M) * n_steps / dt, dt
+    return (1 << M) * len(steps) / dt, dt
+
+
+def oracle_rows_rate(cfg, k1, rows: int = 1 << 18):
+    """Fallback sample for a host without room for an FP64 copy of the state:
+    the oracle's single-row evaluation k2(i) = k1(x(i)) through all L steps on
+    seeded rows.  Returns (amp-steps/s, seconds)."""
+    import oracle
+    M, steps = cfg["M"], cfg["steps"]
+    r = np.random.default_rng(7).integers(0, 1 << M, size=rows, dtype=np.uint64)
+    t0 = time.perf_counter()
+    oracle.sample_outputs(M, lambda src: k1[src], steps, r)
+    dt = time.perf_counter() - t0
+    return rows * len(steps) / dt, dt
 
 
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
+    import oracle
+    oracle.build()
     cfg = workload(args.workload)
-    M = cfg["M"]
-    k1 = W.random_state(M, cfg["dtype"], cfg["state_seed"])
-    per = max(1, min(len(cfg["steps"]), args.ref_steps_per_step))
+    M, steps = cfg["M"], cfg["steps"]
+    L = len(steps)
+    per = args.ref_steps_per_step if args.ref_steps_per_step > 0 else (1 if M >= 31 else 2)
+    per = max(1, min(L, per))
+    k = oracle_state(cfg)
+    if k is None:
+        raise SystemExit("host memory too small for the oracle's FP64 copy of the state")
+    pos = 0
+
+    def one():
+        nonlocal pos
+        sl = [steps[(pos + j) % L] for j in range(per)]
+        pos = (pos + per) % L
+        return oracle_steps_rate(M, k, np.array(sl, dtype=steps.dtype))[1]
+
     for _ in range(args.warmup):
-        oracle_sample_rate(cfg, per, k1)
-    times = []
-    for _ in range(args.steps):
-        _, dt = oracle_sample_rate(cfg, per, k1)
-        times.append(dt)
-    total = sum(times)
+        one()
+    total = sum(one() for _ in range(args.steps))
     value = (1 << M) * per * args.steps / total
-    sample = "first %d of the %d circuit steps on the full 2^%d-amplitude state, per timed step" % (
-        per, len(cfg["steps"]), M)
+    sample = ("%d successive circuit steps per timed step (cycling through the %d steps) on the "
+              "full 2^%d-amplitude state in FP64, in place" % (per, L, M))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128" if np.dtype(cfg["dtype"]) == np.complex128 else "c64",
-        "data": "synthetic", "config": {"workload": cfg["name"], "M": M, "L": len(cfg["steps"])},
+        "data": "synthetic", "config": {"workload": cfg["name"], "M": M, "L": L},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -265,38 +309,65 @@ def run_reference(args, rank, ws):
 # our arm
 # ----------------------------------------------------------------------------
 
-def run_ours(args, rank, ws, local):
+def _roofline(passes, wl_name):
+    """Roofline record of the dominant kernel (most device time) of a list of
+    traced passes (kernel, ms, algorithmic bytes)."""
+    by_kind = {}
+    for kind, ms, by in passes:
+        a = by_kind.setdefault(kind, [0, 0.0, 0.0])
+        a[0] += 1
+        a[1] += ms
+        a[2] += by
+    dkernel, (dlaunch, dms, dbytes) = max(by_kind.items(), key=lambda kv: kv[1][1])
+    peak, peak_src = hbm_peak()
+    achieved = (dbytes / dlaunch) / (dms / dlaunch * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dkernel, wl_name), "kernel": dkernel,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6800 GB/s",
+                "algorithmic_bytes_per_launch": dbytes / dlaunch,
+                "avg_launch_ms": dms / dlaunch, "launches": dlaunch,
+                "share_of_device_time": dms / max(1e-30, sum(v[1] for v in by_kind.values()))}
+    kernel_ms = {k: v[1] / max(1, v[0]) for k, v in by_kind.items()}
+    kernel_launches = {k: v[0] for k, v in by_kind.items()}
+    return roofline, kernel_ms, kernel_launches
+
+
+class Resident:
+    """One workload timed with its state resident in HBM: the context, its
+    host input and what the timed region measured."""
+
+
+def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, sample_clocks=True):
+    """Time steps_k steps of one workload on a resident state (after warmup
+    untimed steps), CUDA events on the context's stream, max over ranks.
+
+    A step is one pass of the whole hot path: validate and plan the circuit,
+    every pass, and the FP64 probabilities into device memory (written by the
+    last pass, or by their own pass with --separate-probs)."""
     import torch
-    from paper_quant_ph_0308158_gb300 import Simulator, build
+    from paper_quant_ph_0308158_gb300 import Simulator
 
-    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
-    build.build()
-    torch.cuda.set_device(local)
-    cfg = workload(args.workload)
+    r = Resident()
     M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
-    L = len(steps)
     n = 1 << M
-    amp = dtype.itemsize
-    strategy = args.strategy or strategy_for(args.workload)
     tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
-
     # seeded state in pinned host memory (also the e2e input buffer), or the
     # qubits of a product-state input generated on the device (App. 1); the
     # end-to-end leg copies that state in from the host all the same
     qubits = cfg.get("qubits")
     h_in = None
     if qubits is None or not args.no_e2e:
-        h_in_t = torch.empty(n, dtype=tdt, pin_memory=True)
-        h_in = h_in_t.numpy()
+        h_in = torch.empty(n, dtype=tdt, pin_memory=True).numpy()
         if qubits is None:
             W.random_state(M, dtype, cfg["state_seed"], out=h_in)
         else:  # the only product-state workload is the Sec. 4 alternating input
             assert np.array_equal(qubits, W.sec4_qubits(M)), "host copy of this product state"
             W.alternating_state(M, dtype, out=h_in)
-    # pinned buffers for the end-to-end leg's probabilities, taken early
-    # (copies from pinned memory taken after host memory has churned can be
-    # far slower)
-    e2e_outs = None if args.no_e2e else torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
+    scratch = strategy in ("auto", "gather")  # the other strategies work in place
+    sim = Simulator(M, dtype, scratch=scratch)
+    sim.set_strategy(strategy, args.tile_bits, args.low_bits)
+    sim.set_canonicalize(False)
 
     def load_input():
         if qubits is None:
@@ -304,17 +375,12 @@ def run_ours(args, rank, ws, local):
         else:
             sim.load_product_state(qubits)
 
-    scratch = strategy in ("auto", "gather")  # the other strategies work in place
-    sim = Simulator(M, dtype, scratch=scratch)
-    sim.set_strategy(strategy, args.tile_bits, args.low_bits)
-    sim.set_canonicalize(False)
     jit_ms = None
-    if args.jit and scratch:
+    if use_jit and scratch:
         from paper_quant_ph_0308158_gb300 import jit_precompile
         jit_ms = jit_precompile(M, dtype, steps, canonicalize=False)
         sim.set_jit(True)
     probs = torch.empty(n, dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
     tuned = None
     if args.autotune:  # measured plan choice, before warm-up (not timed, like compilation)
         load_input()
@@ -329,139 +395,184 @@ def run_ours(args, rank, ws, local):
         else:
             sim.apply_probabilities(steps, probs.data_ptr())
 
-    # ---- device-resident timing ------------------------------------------------
+    stream = torch.cuda.current_stream()
     load_input()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     sim.synchronize()
     sim.set_profiling(True)
     sim.pass_times()  # clear
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks = ClockSampler(local) if sample_clocks else None
+    if clocks:
+        clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps_k):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
-    clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
+    r.clocks = clocks.stop() if clocks else None
+    ms_total = max_over_ranks(e0.elapsed_time(e1), ws)
     passes = sim.pass_times()
     sim.set_profiling(False)
-    stats = sim.plan_stats()
-    ms_total = max_over_ranks(ms_total, ws)
-    ms_step = ms_total / args.steps
-    value = ws * n * L * args.steps / (ms_total * 1e-3)
+    r.stats = sim.plan_stats()
+    r.ms_step = ms_total / steps_k
+    r.value = ws * n * len(steps) * steps_k / (ms_total * 1e-3)
+    r.roofline, r.kernel_ms, r.kernel_launches = _roofline(passes, cfg["name"])
+    r.launches = len(passes)  # every pass kernel and probabilities kernel in the timed region
+    r.sim, r.h_in, r.qubits, r.scratch, r.jit_ms, r.tuned, r.probs = sim, h_in, qubits, scratch, jit_ms, tuned, probs
+    return r
 
-    # dominant kernel (most device time in the timed region)
-    by_kind = {}
-    for kind, ms, by in passes:
-        a = by_kind.setdefault(kind, [0, 0.0, 0.0])
-        a[0] += 1
-        a[1] += ms
-        a[2] += by
-    dom = max(by_kind.items(), key=lambda kv: kv[1][1])
-    dkernel, (dlaunch, dms, dbytes) = dom
-    peak, peak_src = hbm_peak()
-    achieved = (dbytes / dlaunch) / (dms / dlaunch * 1e-3) / 1e9
-    traffic = ncu_traffic(dkernel, cfg["name"])
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": dkernel,
-                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                else "fallback 6800 GB/s",
-                "algorithmic_bytes_per_launch": dbytes / dlaunch,
-                "avg_launch_ms": dms / dlaunch, "launches": dlaunch}
 
-    # ---- end to end through the C ABI with host buffers ----------------------
-    e2e = None
-    if not args.no_e2e:
-        # Each step copies its state in from pinned host memory, applies the
-        # circuit and copies its FP64 probabilities out, all through the C ABI.
-        # Two contexts on two streams alternate steps, so one step's copies
-        # overlap the other's kernels (each context waits for its previous
-        # step before reusing its buffers).
-        h2d = n * amp
-        d2h = n * 8
-        s2 = torch.cuda.Stream()
-        with torch.cuda.stream(s2):
-            sim2 = Simulator(M, dtype, scratch=scratch)
-        sim2.set_strategy(strategy, args.tile_bits, args.low_bits)
-        sim2.set_canonicalize(False)
-        if jit_ms is not None:
-            sim2.set_jit(True)
-        sims = (sim, sim2)
-        streams = (stream, s2)
-        outs = [e2e_outs[:n], e2e_outs[n:]]
+def measure_e2e(args, cfg, r, local, ws, steps_k):
+    """The same metric end to end through the C ABI with host buffers: each
+    step copies its state in from pinned host memory, applies the circuit and
+    copies the FP64 probabilities out to pinned host memory.  Two contexts on
+    two streams alternate steps, so one step's copies overlap the other's
+    kernels (each context waits for its previous step before reusing its
+    buffers); copies in go one after the other over the host link."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Simulator
 
-        loaded = [torch.cuda.Event() for _ in range(2)]
+    M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
+    n = 1 << M
+    L = len(steps)
+    outs_block = torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
+    stream = torch.cuda.current_stream()
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        sim2 = Simulator(M, dtype, scratch=r.scratch)
+    sim2.set_strategy(args.strategy or strategy_for(args.workload), args.tile_bits, args.low_bits)
+    sim2.set_canonicalize(False)
+    if r.jit_ms is not None:
+        sim2.set_jit(True)
+    sims = (r.sim, sim2)
+    streams = (stream, s2)
+    outs = [outs_block[:n].numpy(), outs_block[n:].numpy()]
+    loaded = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step(i):
-            c = i & 1
-            sm = sims[c]
-            if i >= 2:
-                sm.synchronize()  # this context's previous step is done
-            if i >= 1:  # copies in go one after the other over the host link
-                streams[c].wait_event(loaded[1 - c])
-            sm.load_state_async(h_in)
-            loaded[c].record(streams[c])
-            sm.apply_probabilities_async(steps, outs[c].numpy())
+    def e2e_step(i):
+        c = i & 1
+        sm = sims[c]
+        if i >= 2:
+            sm.synchronize()  # this context's previous step is done
+        if i >= 1:  # copies in go one after the other over the host link
+            streams[c].wait_event(loaded[1 - c])
+        sm.load_state_async(r.h_in)
+        loaded[c].record(streams[c])
+        sm.apply_probabilities_async(steps, outs[c])
 
-        for i in range(2):  # warm both contexts
-            e2e_step(i)
-        for sm in sims:
-            sm.synchronize()
-        torch.cuda.synchronize()
-        barrier(ws)
-        f0 = torch.cuda.Event(enable_timing=True)
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ke = max(2, args.steps)
-        f0.record(stream)
-        s2.wait_event(f0)
-        for i in range(ke):
-            e2e_step(i)
-        for sm in sims:
-            sm.synchronize()
-        for j in range(2):
-            ends[j].record(streams[j])
-        torch.cuda.synchronize()
-        ms_e2e = max_over_ranks(max(f0.elapsed_time(e) for e in ends), ws)
-        e2e = {"value": ws * n * L * ke / (ms_e2e * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": ms_e2e / ke,
-               "pipelining": "two contexts on two streams alternate steps; copies in are serialised"}
-        sim2.close()
-        del outs
+    for i in range(2):  # warm both contexts
+        e2e_step(i)
+    for sm in sims:
+        sm.synchronize()
+    torch.cuda.synchronize()
+    barrier(ws)
+    f0 = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ke = max(2, steps_k)
+    f0.record(stream)
+    s2.wait_event(f0)
+    for i in range(ke):
+        e2e_step(i)
+    for sm in sims:
+        sm.synchronize()
+    for j in range(2):
+        ends[j].record(streams[j])
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(max(f0.elapsed_time(e) for e in ends), ws)
+    sim2.close()
+    del outs, outs_block
+    return {"value": ws * n * L * ke / (ms_e2e * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": n * dtype.itemsize, "d2h_bytes_per_step": n * 8,
+            "ms_per_step": ms_e2e / ke, "steps": ke,
+            "pipelining": "two contexts on two streams alternate steps; copies in are serialised"}
+
+
+def cpu_baseline_for(args, cfg, h_in):
+    """The oracle, as it stands, on the first steps of the same circuit and
+    state (single thread, full state in FP64, widened before timing)."""
+    import oracle
+    oracle.build()
+    M, steps = cfg["M"], cfg["steps"]
+    L = len(steps)
+    nst = min(L, args.cpu_steps if args.cpu_steps > 0 else (2 if M >= 31 else 24))
+    k = oracle_state(cfg, h_in)
+    if k is None:
+        rate, secs = oracle_rows_rate(cfg, h_in)
+        sample = ("host too small for a %d GiB FP64 copy: single-row evaluation of all %d steps "
+                  "on 2^18 seeded rows (%.1f s)" % ((16 << M) >> 30, L, secs))
+    else:
+        rate, secs = oracle_steps_rate(M, k, steps[:nst])
+        sample = "first %d of the %d steps on the full 2^%d-amplitude state, FP64 (%.1f s)" % (
+            nst, L, M, secs)
+    del k
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "host_threads": os.cpu_count()}
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_quant_ph_0308158_gb300 import build
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    build.build()
+    torch.cuda.set_device(local)
+    cfg = workload(args.workload)
+    M, dtype, L = cfg["M"], np.dtype(cfg["dtype"]), len(cfg["steps"])
+    n = 1 << M
+    strategy = args.strategy or strategy_for(args.workload)
+    r = measure_resident(args, cfg, strategy, args.jit, local, ws, args.steps, args.warmup)
 
     # ---- CPU baseline: the oracle on a bounded prefix (rank 0, N=1) -----------
+    # (before the end-to-end leg, whose pinned buffers stay cached)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and h_in is not None:
-        nst = min(L, args.cpu_steps)
-        rate, secs = oracle_sample_rate(cfg, nst, h_in)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d of the %d steps on the full 2^%d-amplitude state (%.1f s)" % (
-                   nst, L, M, secs)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and r.h_in is not None:
+        cpu = cpu_baseline_for(args, cfg, r.h_in)
 
-    launches = len(passes)  # every pass kernel and probabilities kernel in the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, cfg, r, local, ws, args.steps)
+    h_in_bytes = 0 if r.h_in is None else r.h_in.nbytes
+    r.sim.close()
+    r.h_in = None
+    del r.probs
+
+    # ---- the other single-circuit workload, on the same line ------------------
+    also = {}
+    for wl in args.also:
+        if wl == args.workload:
+            continue
+        c2 = workload(wl)
+        r2 = measure_resident(args, c2, strategy_for(wl), args.jit, local, ws, args.steps,
+                              args.warmup, sample_clocks=False)
+        r2.sim.close()
+        also[wl] = {"workload": c2["name"], "value": r2.value, "unit": UNIT,
+                    "ms_per_step": r2.ms_step, "M": c2["M"], "L": len(c2["steps"]),
+                    "dtype": "c128" if np.dtype(c2["dtype"]) == np.complex128 else "c64",
+                    "passes_per_step": r2.stats["passes"], "jit": r2.jit_ms is not None,
+                    "jit_compile_ms": r2.jit_ms, "kernel_ms": r2.kernel_ms,
+                    "roofline": r2.roofline, "gpu_launches": r2.launches}
 
     # ---- batched vs one launch per circuit (part of the metric) ----------------
     batch = None
     if not args.no_batch:
-        sim.close()
-        batch = batch_speedup(args.batch_compare, "cnot", 10, 3)
+        batch = [batch_speedup(args.batch_compare, mix, 10, 3) for mix in ("cnot", "mixed")]
     if rank == 0:
+        stats = r.stats
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "metric": METRIC, "value": r.value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if dtype == np.complex128 else "c64",
             "data": "synthetic (seeded random state and circuit)",
             "config": {"workload": cfg["name"], "M": M, "L": L, "strategy": strategy,
                        "tile_bits": args.tile_bits, "low_bits": args.low_bits,
-                       "state_bytes": n * amp, "l2": "inputs larger than L2",
+                       "state_bytes": n * dtype.itemsize, "l2": "inputs larger than L2",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "passes_per_step": stats["passes"],
                        "gather_passes": stats["gather_passes"],
@@ -472,19 +583,21 @@ def run_ours(args, rank, ws, local):
                        "step_includes": "plan + all passes + FP64 probabilities",
                        "probabilities": "separate pass" if args.separate_probs
                        else "written by the last pass",
-                       "jit": bool(jit_ms is not None),
-                       "autotune": tuned,
-                       "jit_compile_ms": jit_ms,
-                       "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in by_kind.items()}},
-            "roofline": roofline,
+                       "in_place": not r.scratch,
+                       "jit": bool(r.jit_ms is not None),
+                       "autotune": r.tuned,
+                       "jit_compile_ms": r.jit_ms,
+                       "host_input_bytes": h_in_bytes,
+                       "kernel_ms": r.kernel_ms, "kernel_launches": r.kernel_launches},
+            "roofline": r.roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
+            "gpu_launches": r.launches,
+            "clocks": r.clocks,
+            "also": also or None,
             "batch": batch,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
     return 0
 
 
@@ -808,7 +921,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed_m28", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
+    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
                              "batch_cnot", "batch_mixed", "serve", "parity_scan"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
@@ -834,18 +947,23 @@ def main():
                     help="time candidate plans first and keep the fastest (qsim_autotune)")
     ap.add_argument("--scan-m-min", type=int, default=16)
     ap.add_argument("--scan-m-max", type=int, default=33)
-    ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for cpu_baseline")
-    ap.add_argument("--ref-steps-per-step", type=int, default=2,
-                    help="oracle steps per timed reference step")
+    ap.add_argument("--cpu-steps", type=int, default=0,
+                    help="oracle steps for cpu_baseline (0: 2 at M >= 31, else 24)")
+    ap.add_argument("--ref-steps-per-step", type=int, default=0,
+                    help="oracle steps per timed reference step (0: 1 at M >= 31, else 2)")
     ap.add_argument("--no-jit", dest="jit", action="store_false",
                     help="use the general bit-sliced gather instead of compiled kernels")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison of the default run")
-    ap.add_argument("--batch-compare", type=int, default=1024,
+    ap.add_argument("--also", default="mixed_m28",
+                    help="comma-separated single-circuit workloads also timed on the same line "
+                         "(device-resident, no e2e); empty: none")
+    ap.add_argument("--batch-compare", type=int, default=4096,
                     help="circuits in the default run's batched-vs-plain comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    args.also = [w for w in args.also.split(",") if w]
     if args.warmup < 3 and args.impl == "ours":
         print("note: timing rules want >= 3 warm-up steps", file=sys.stderr)
     rank, ws, local = dist_init()

@@ -227,6 +227,17 @@ int qsim_set_jit(qsim_ctx *ctx, int enable);
 int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L, int canonicalize,
                         double *compile_ms);
 
+/* Testing hook for failure handling (no counterpart in the paper).  Arms the
+ * next tile pass of this context only: its producer warp leaves before
+ * issuing any copy, and the consumers' pipeline waits (mbarrier polls) give
+ * up after poll_limit polls instead of the default of about 2^24, so every
+ * wait runs out with no bulk copy in flight.  That pass changes no amplitude
+ * and sets the context's error flag; the next qsim_synchronize or
+ * qsim_read_state returns QSIM_ETIMEOUT and clears the flag, and the context
+ * stays usable.  poll_limit must be in [1, 2^20] (QSIM_EINVAL otherwise).  A
+ * pass that is not a tile pass leaves the hook armed. */
+int qsim_set_wait_test(qsim_ctx *ctx, uint32_t poll_limit);
+
 /* Adjacent equal steps cancel in pairs (each step is its own inverse,
  * Sec. 2a).  enable = 1 (default) removes them before planning; 0 applies
  * every step as given. */
@@ -392,7 +403,10 @@ int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const 
 
 /* *done = 1 once the probabilities are in the result arena; then
  * *latency_ms (may be NULL) is submit-to-result time and *probs (may be NULL)
- * points at the 2^M FP64 probabilities, valid until qsim_server_release. */
+ * points at the 2^M FP64 probabilities, valid until qsim_server_release.
+ * A request whose uploads could not be queued at admission (a failed CUDA
+ * call) holds no memory and is complete but failed: poll returns QSIM_ECUDA
+ * with the reason in qsim_last_error(), and it still needs releasing. */
 int qsim_server_poll(qsim_server *s, uint64_t req_id, int *done, double *latency_ms,
                      const double **probs);
 
@@ -488,10 +502,14 @@ int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, i
  * library holds it until the process exits.  The launch never uses more
  * than 1024 blocks, so every M in [1, QSIM_MAX_QUBITS] fits; M outside that
  * range, an unknown dtype, a NULL d_state/d_norm or a misaligned pointer
- * returns QSIM_EINVAL with a message in qsim_last_error().  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture on the
- * device.  All calls share the one array and every call overwrites it, so
+ * returns QSIM_EINVAL with a message in qsim_last_error().  Every call looks
+ * up the array's device address (cudaGetSymbolAddress) in the CUDA context
+ * current on the calling thread, so a later context on the same device or a
+ * device reset leaves no stale address.  The first call in a context may load
+ * the library's device code into it (CUDA loads modules lazily), and that load
+ * reserves device memory for the module: make the first call (or any other
+ * launch of this library) at start-up, while memory is still free, and before
+ * any stream capture.  After that, a call allocates nothing.  All calls share the one array and every call overwrites it, so
  * calls whose work overlaps on the GPU (different streams, or several host
  * threads) race: serialise them.  Calls no cudaMalloc, cudaFree or other
  * allocating routine. */

@@ -117,6 +117,16 @@ def apply_circuit(M: int, k1: np.ndarray, steps) -> np.ndarray:
     return k
 
 
+def apply_circuit_inplace(M: int, k: np.ndarray, steps) -> np.ndarray:
+    """apply_circuit on a complex128 state the caller owns, in place (no copy):
+    the same C loop, for timing the oracle on states too large to copy."""
+    s = _steps(steps)
+    if k.dtype != np.complex128 or k.shape != (1 << M,) or not k.flags.c_contiguous:
+        raise ValueError("state must be a contiguous complex128 array of length 2^M")
+    _check(_load().oracle_apply_circuit(M, _ptr(k), _ptr(s), len(s)), "apply_circuit")
+    return k
+
+
 def step_row_array(M: int, step) -> np.ndarray:
     """Row array y(i) of one step, built by the +/-2^(goto-1) toggles (Sec. 2b-2d)."""
     s = _steps(np.asarray([step], dtype=STEP_DTYPE) if np.ndim(step) == 0 else step)

@@ -45,6 +45,7 @@ EXPORTS = (
     "qsim_apply_circuit_probabilities", "qsim_apply_circuit_probabilities_async", "qsim_autotune",
     "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
+    "qsim_set_wait_test",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
@@ -150,6 +151,7 @@ def load() -> ctypes.CDLL:
             "qsim_set_canonicalize": ([p, i], i),
             "qsim_set_profiling": ([p, i], i),
             "qsim_set_jit": ([p, i], i),
+            "qsim_set_wait_test": ([p, u32], i),
             "qsim_jit_precompile": ([u32, i, p, sz, i, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_get_pass_times": ([p, p, p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_get_plan_stats": ([p, ctypes.POINTER(PlanStats)], i),
@@ -348,6 +350,10 @@ class Simulator:
 
     def set_jit(self, enable: bool):
         _check(self._lib.qsim_set_jit(self._ctx, int(bool(enable))))
+
+    def set_wait_test(self, poll_limit: int):
+        """Arm the next tile pass to give up its pipeline waits (testing)."""
+        _check(self._lib.qsim_set_wait_test(self._ctx, poll_limit))
 
     def set_canonicalize(self, enable: bool):
         _check(self._lib.qsim_set_canonicalize(self._ctx, int(bool(enable))))

@@ -194,6 +194,8 @@ struct TileKParams {
     uint32_t affine;               // every step has at most one control
     uint32_t start[6];             // tensor view: first address bit of each dimension
     uint32_t rest_pos[kMaxHighBits];
+    uint32_t wait_limit;           // polls before a pipeline wait gives up
+    uint32_t stall_producer;       // testing: the producer leaves without loading a tile
 };
 
 struct TileStageMeta {
@@ -219,9 +221,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait on an mbarrier phase; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
-    for (unsigned w = 0; w < kWaitLimit; ++w)
+    for (unsigned w = 0; w < limit; ++w)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -280,13 +282,16 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
 
     if (warp == kTileThreads / 32) {
         // ---------------- producer warp ----------------
+        // testing hook: leave before any copy is issued, so that every
+        // consumer's first wait runs out with nothing in flight
+        if (p.stall_producer) return;
         uint64_t next = begin;
         uint32_t last[kMaskWords];
         bool have_last = false;
         const uint32_t run_bytes = (uint32_t)B << p.l;
         for (uint32_t it = 0;; ++it) {
             const uint32_t s = it % p.stages;
-            if (it >= p.stages && !mbar_wait_bounded(&empty[s], ((it / p.stages) - 1) & 1u)) {
+            if (it >= p.stages && !mbar_wait_bounded(&empty[s], ((it / p.stages) - 1) & 1u, p.wait_limit)) {
                 if (lane == 0) atomicOr(p.err, 2);
                 return;
             }
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     A *st = reinterpret_cast<A *>(p.state);
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
-        if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u)) {
+        if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u, p.wait_limit)) {
             if (tid == 0) atomicOr(p.err, 1);
             return;
         }
@@ -927,9 +932,11 @@ size_t tile_smem_bytes(int amp_bytes, int k)
 }
 
 int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d_steps,
-                int *d_err, double *d_probs, void *stream)
+                int *d_err, double *d_probs, void *stream, const WaitTest *wt)
 {
     TileKParams p;
+    p.wait_limit = (wt && wt->poll_limit) ? wt->poll_limit : kWaitLimit;
+    p.stall_producer = (wt && wt->stall_producer) ? 1u : 0u;
     p.state = static_cast<char *>(state);
     p.probs = d_probs;
     p.steps = d_steps + t.step_off;

@@ -9,12 +9,18 @@
 // partial sums), so those callers use qsim_probabilities_noalloc instead.  The
 // only scratch memory it needs -- the per-block partial sums of the norm
 // reduction -- lives in the fixed array below, which every GPU that loads this
-// library holds until the process exits.  The first call on a device resolves
-// the array's device address and should come before any stream capture on
-// that device; calls whose work overlaps on the GPU share the array and race.
+// library holds until the process exits.  Every call resolves the array's
+// device address afresh in the CUDA context that is current (after the first
+// resolution in a context this is a lookup that allocates nothing), so a
+// context created later on the same device, or a device reset, never leaves a
+// stale address behind.  The first call in a context may load this library's
+// device code into it (CUDA loads modules lazily by default), and that load
+// reserves the module's device memory: make that first call, or any other
+// launch of this library, while memory is still available -- at start-up, and
+// before any stream capture.  Calls whose work overlaps on the GPU share the
+// array and race.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "qsim_internal.h"
@@ -25,10 +31,6 @@ namespace {
 // many blocks, whatever the state size.
 constexpr int kNoAllocPartials = 1024;
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_partials_ptr[kMaxDevices] = {nullptr};
 
 int noalloc_fail(int code, const std::string &msg)
 {
@@ -53,25 +55,14 @@ extern "C" int qsim_probabilities_noalloc(const void *d_state, uint32_t M, int d
     if (qsim::probabilities_partials_needed() > kNoAllocPartials)
         return noalloc_fail(QSIM_EINVAL, "reduction needs more partial sums than the fixed scratch");
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(QSIM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(QSIM_EINVAL, "device index too large");
-    double *partials = nullptr;
-    {
-        // First call on this device: resolve the array's device address with
-        // this device current.  The host-side name g_noalloc_partials is only a
-        // stand-in and must never reach a kernel.
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_partials_ptr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess)
-                return noalloc_fail(QSIM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_partials_ptr[dev] = static_cast<double *>(p);
-        }
-        partials = g_partials_ptr[dev];
-    }
+    // Resolve the array's device address in the current context.  The
+    // host-side name g_noalloc_partials is only a stand-in and must never
+    // reach a kernel.
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess)
+        return noalloc_fail(QSIM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    double *partials = static_cast<double *>(p);
     // Every block writes its partial before the final reduction reads it, so
     // nothing left over from an earlier call is ever read.
     const int rc = qsim::launch_probabilities(d_state, amp, 1ull << M, d_probs, partials,

@@ -79,6 +79,9 @@ struct qsim_ctx {
     std::vector<cudaEvent_t> ev;        // 2 per pass
     std::vector<uint32_t> prof_kinds;
     std::vector<double> prof_bytes;
+    // testing hook for the next tile pass (qsim_set_wait_test), then cleared
+    WaitTest wait_test;
+    bool wait_test_armed = false;
 };
 
 namespace {
@@ -395,6 +398,16 @@ int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L,
     return QSIM_OK;
 }
 
+int qsim_set_wait_test(qsim_ctx *c, uint32_t poll_limit)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    if (poll_limit == 0 || poll_limit > (1u << 20)) return fail(QSIM_EINVAL, "poll_limit must be in [1, 2^20]");
+    c->wait_test.poll_limit = poll_limit;
+    c->wait_test.stall_producer = true;
+    c->wait_test_armed = true;
+    return QSIM_OK;
+}
+
 int qsim_set_canonicalize(qsim_ctx *c, int enable)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
@@ -520,7 +533,9 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
         if (p.kind == kSweep) {
             e = launch_sweep(c->buf[c->cur], (int)c->amp, p.sweep, c->d_err, c->stream);
         } else if (p.kind == kTile) {
-            e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, pp, c->stream);
+            e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, pp, c->stream,
+                            c->wait_test_armed ? &c->wait_test : nullptr);
+            c->wait_test_armed = false;
         } else if (p.gather.jit) {
             std::string jmsg;
             const int jrc = launch_jit_gather(c->buf[c->cur], c->buf[1 - c->cur], (int)c->amp, c->M,

@@ -175,8 +175,16 @@ void set_last_error(const std::string &msg);
 // d_probs makes a tile or gather pass also write the FP64 probabilities of
 // the state it leaves (2^M doubles).
 int launch_sweep(void *state, int amp_bytes, const SweepParams &p, int *d_err, void *stream);
+// Testing hook for the tile pipeline's bounded waits (qsim_set_wait_test):
+// poll_limit polls before a wait gives up (0: the default, seconds), and a
+// producer warp that leaves before issuing any copy (the hook always sets
+// both, so no wait gives up while a copy is in flight).
+struct WaitTest {
+    uint32_t poll_limit = 0;
+    bool stall_producer = false;
+};
 int launch_tile(void *state, int amp_bytes, const TilePass &p, const TileStep *d_steps,
-                int *d_err, double *d_probs, void *stream);
+                int *d_err, double *d_probs, void *stream, const WaitTest *wt = nullptr);
 int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &p,
                   const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err, double *d_probs,
                   void *stream);

@@ -76,6 +76,8 @@ struct Request {
     cudaEvent_t up0 = nullptr, down0 = nullptr;  // timing: starts of the two copies
     Clock::time_point t_submit, t_admit, t_done;
     size_t host_bytes = 0;
+    bool failed = false;     // admission failed: no memory held, 'error' says why
+    std::string error;
 };
 
 }  // namespace
@@ -159,12 +161,35 @@ void block_sizes(const Plan &p, uint32_t M, size_t amp, size_t out[2])
 constexpr size_t kMaxPendingUpload = 8ull << 30;
 
 // Try to admit waiting request r; called with the lock held.
-bool try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
+// Outcome of one admission attempt.
+enum Admit { kNotAdmitted, kAdmitted, kAdmitFailed };
+
+// An admitted request whose uploads could not be queued: give back both
+// device blocks and the host block and complete it as failed, so that it
+// never runs on memory it did not fill.  Called with the lock held.
+Admit fail_admission(qsim_server *s, const std::shared_ptr<Request> &r, const char *what,
+                     cudaError_t e)
+{
+    for (int b = 0; b < 2; ++b)
+        if (r->held[b]) {
+            s->dev.release(r->off[b]);
+            r->held[b] = false;
+        }
+    s->host.release(r->host_off);
+    r->failed = true;
+    r->error = std::string(what) + ": " + cudaGetErrorString(e);
+    r->state = Request::kDone;
+    r->t_done = Clock::now();
+    s->completions.push_back(r->id);
+    return kAdmitFailed;
+}
+
+Admit try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
 {
     const size_t n = 1ull << r->M;
     // a request is admitted when the uploads already queued are short, so
     // that its memory is not held while it waits for the copy stream
-    if (s->pending_upload_bytes >= kMaxPendingUpload) return false;
+    if (s->pending_upload_bytes >= kMaxPendingUpload) return kNotAdmitted;
     size_t sl_off = 0;
     const size_t tb = tables_bytes(r->plan, &sl_off);
     block_sizes(r->plan, r->M, s->amp, r->bytes);
@@ -173,15 +198,15 @@ bool try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
     // reached it
     r->host_bytes = align256(n * 8) + tb;
     size_t hoff = 0;
-    if (!s->dev.alloc(r->bytes[0], &r->off[0])) return false;
+    if (!s->dev.alloc(r->bytes[0], &r->off[0])) return kNotAdmitted;
     if (!s->dev.alloc(r->bytes[1], &r->off[1])) {
         s->dev.release(r->off[0]);
-        return false;
+        return kNotAdmitted;
     }
     if (!s->host.alloc(r->host_bytes, &hoff)) {
         s->dev.release(r->off[0]);
         s->dev.release(r->off[1]);
-        return false;
+        return kNotAdmitted;
     }
     r->held[0] = r->held[1] = true;
     r->host_off = hoff;
@@ -197,22 +222,28 @@ bool try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
     if (!r->plan.sliced_steps.empty())
         std::memcpy(h_tab + sl_off, r->plan.sliced_steps.data(),
                     r->plan.sliced_steps.size() * sizeof(SlicedStep));
-    cudaEventRecord(r->up0, s->h2d);
+    cudaError_t e = cudaEventRecord(r->up0, s->h2d);
+    if (e != cudaSuccess) return fail_admission(s, r, "cudaEventRecord(upload start)", e);
     const auto e0 = Clock::now();
-    cudaMemcpyAsync(r->buf[0], r->host_in, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
-    if (tb) cudaMemcpyAsync(r->d_tab, h_tab, tb, cudaMemcpyHostToDevice, s->h2d);
+    e = cudaMemcpyAsync(r->buf[0], r->host_in, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
+    if (e != cudaSuccess) return fail_admission(s, r, "cudaMemcpyAsync(state upload)", e);
+    if (tb) {
+        e = cudaMemcpyAsync(r->d_tab, h_tab, tb, cudaMemcpyHostToDevice, s->h2d);
+        if (e != cudaSuccess) return fail_admission(s, r, "cudaMemcpyAsync(plan tables)", e);
+    }
     // a copy from memory the driver does not see as pinned runs on this
     // thread (and stalls the scheduler): record how long issuing took
     const double enq = std::chrono::duration<double, std::milli>(Clock::now() - e0).count();
     s->st.issue_ms += enq;
     s->st.issue_ms_max = std::max(s->st.issue_ms_max, enq);
-    cudaEventRecord(r->uploaded, s->h2d);
+    e = cudaEventRecord(r->uploaded, s->h2d);
+    if (e != cudaSuccess) return fail_admission(s, r, "cudaEventRecord(uploaded)", e);
     s->st.h2d_bytes += n * s->amp;
     s->pending_upload_bytes += n * s->amp;
     r->state = Request::kUploading;
     s->active.push_back(r);
     ++s->st.admitted;
-    return true;
+    return kAdmitted;
 }
 
 // Admission: FIFO, except that while the head of the queue does not fit and
@@ -223,15 +254,16 @@ void admit(qsim_server *s)
 {
     constexpr size_t kWindow = 256;  // requests looked at behind the head
     if (s->paused) return;
-    while (!s->waiting.empty() && try_admit(s, s->waiting.front())) s->waiting.pop_front();
+    while (!s->waiting.empty() && try_admit(s, s->waiting.front()) != kNotAdmitted) s->waiting.pop_front();
     if (s->waiting.empty() || s->max_head_wait_ms < 0) return;
     const double head_wait =
         std::chrono::duration<double, std::milli>(Clock::now() - s->waiting.front()->t_submit).count();
     if (head_wait >= s->max_head_wait_ms) return;
     size_t looked = 0;
     for (auto it = std::next(s->waiting.begin()); it != s->waiting.end() && looked < kWindow; ++looked) {
-        if (try_admit(s, *it)) {
-            ++s->st.backfilled;
+        const Admit a = try_admit(s, *it);
+        if (a != kNotAdmitted) {
+            if (a == kAdmitted) ++s->st.backfilled;
             it = s->waiting.erase(it);
         } else {
             ++it;
@@ -574,6 +606,7 @@ int qsim_server_poll(qsim_server *s, uint64_t id, int *done, double *latency_ms,
     if (it == s->all.end()) return sfail(QSIM_ENOTFOUND, "unknown request id");
     const auto &r = it->second;
     *done = r->state == Request::kDone;
+    if (r->failed) return sfail(QSIM_ECUDA, "request " + std::to_string(id) + " failed: " + r->error);
     if (*done) {
         if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
         if (probs) *probs = reinterpret_cast<const double *>(s->h_arena + r->host_off);
@@ -607,7 +640,7 @@ int qsim_server_release(qsim_server *s, uint64_t id)
     auto it = s->all.find(id);
     if (it == s->all.end()) return sfail(QSIM_ENOTFOUND, "unknown request id");
     if (it->second->state != Request::kDone) return sfail(QSIM_EBUSY, "request still running");
-    s->host.release(it->second->host_off);
+    if (!it->second->failed) s->host.release(it->second->host_off);  // a failed one gave it back
     cudaEventDestroy(it->second->uploaded);
     cudaEventDestroy(it->second->computed);
     cudaEventDestroy(it->second->finished);

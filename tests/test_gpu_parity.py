@@ -235,7 +235,14 @@ def test_small_cnot_workload_full_state():
             np.testing.assert_array_equal(got, want)
 
 
-def _sampled_check(cfg, strategy, rows=1 << 20):
+def _sampled_check(cfg, strategy, rows=1 << 20, jit=False, probs=False):
+    """Run a full-size workload through the C ABI and compare sampled output
+    rows bit for bit with the oracle's single-row evaluation k2(i) = k1(x(i))
+    (Sec. 2h product, Sec. 2b gather), plus order-independent sums of the
+    whole state before and after.  With probs the circuit runs through
+    qsim_apply_circuit_probabilities, as the benchmark does, and the sampled
+    FP64 probabilities are compared with the oracle's.  Returns the plan
+    statistics and the kernels that ran."""
     import torch
     M, dtype, steps = cfg["M"], cfg["dtype"], cfg["steps"]
     k1 = W.random_state(M, dtype, cfg["state_seed"])
@@ -244,37 +251,69 @@ def _sampled_check(cfg, strategy, rows=1 << 20):
     r[:4] = [0, 1, (1 << M) - 2, (1 << M) - 1]
     src = oracle.source_rows(M, steps, r).astype(np.int64)
     want = k1[src]
+    ridx = torch.from_numpy(r.astype(np.int64)).cuda()
     with Simulator(M, dtype, scratch=(strategy != "inplace")) as sim:
         sim.set_strategy(strategy)
         sim.set_canonicalize(False)
+        sim.set_jit(jit)
+        sim.set_profiling(True)
         sim.load_state(k1)
         h0 = _device_hash(sim.state_tensor())
-        sim.apply(steps)
+        p_dev = None
+        if probs:
+            p_dev = torch.full((1 << M,), -1.0, dtype=torch.float64, device="cuda")
+            sim.apply_probabilities(steps, p_dev.data_ptr())
+        else:
+            sim.apply(steps)
         sim.synchronize()
+        kernels = [k for k, _, _ in sim.pass_times()]
         t = sim.state_tensor()
-        got = t[torch.from_numpy(r.astype(np.int64)).cuda()].cpu().numpy()
+        got = t[ridx].cpu().numpy()
         h1 = _device_hash(t)
+        got_p = p_dev[ridx].cpu().numpy() if probs else None
         stats = sim.plan_stats()
+        del p_dev
     np.testing.assert_array_equal(got, want)
     assert h0 == h1
-    return stats
+    if probs:
+        want_p = oracle.probabilities(want)
+        if np.dtype(dtype) == np.complex64:  # exact squares: identical bits
+            np.testing.assert_array_equal(got_p.view(np.uint64), want_p.view(np.uint64))
+        else:
+            assert_probs_close(got_p, want_p)
+    return stats, kernels
 
 
 def test_mixed_m28_workload_sampled():
-    """M=28 complex128, 1000 mixed steps: the benchmarked configuration."""
-    st = _sampled_check(W.config_mixed_m28(), "auto")
+    """M=28 complex128, 1000 mixed steps, bit-sliced interpreter
+    (gather_sliced_kernel: compiled kernels off)."""
+    st, kernels = _sampled_check(W.config_mixed_m28(), "auto")
     assert st["gather_passes"] >= 1
+    assert "gather_sliced_kernel" in kernels
+
+
+def test_mixed_m28_benchmarked_launch_sampled():
+    """The benchmarked launch of the M=28 complex128 1000-step mixed workload:
+    compiled gather (qsim_jit_gather), no cancellation, probabilities written
+    by the same pass -- sampled rows bit-exact, probabilities within 1e-12
+    and 2 ulp of the oracle's."""
+    st, kernels = _sampled_check(W.config_mixed_m28(), "auto", jit=True, probs=True)
+    assert st["passes"] == 1 and st["gather_passes"] == 1
+    assert kernels == ["qsim_jit_gather"]
 
 
 def test_mixed_m28_workload_inplace_sampled():
-    st = _sampled_check(W.config_mixed_m28(), "inplace")
+    st, _ = _sampled_check(W.config_mixed_m28(), "inplace")
     assert st["gather_passes"] == 0
 
 
 def test_adder_m32_workload_sampled():
-    """M=32 complex64 (32 GiB) adder, in place."""
-    st = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 18)
+    """M=32 complex64 (32 GiB) adder, in place, as benchmarked: tile passes,
+    the last one also writing the FP64 probabilities (bit-exact for
+    complex64, whose squares are exact)."""
+    st, kernels = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 18, probs=True)
     assert st["gather_passes"] == 0 and st["passes"] >= 1
+    assert set(kernels) <= {"tile_kernel", "sweep_kernel"} and kernels[-1] == "tile_kernel"
 
 
 def test_sec4_parity_m32_from_qubits_with_probabilities(cuda):
