@@ -749,6 +749,74 @@ def serve_plain_baseline(specs, pool):
             "how": "first requests of the same stream, one at a time, closed loop"}
 
 
+def run_gather_floor(args, rank, ws, local):
+    """The random-read floor of the gather pass: the M=28 complex128 mixed
+    circuit's row array (qsim_row_array) applied by qsim_gather_rows -- the
+    same 2^28 scattered 16-byte reads and coalesced stores and probabilities
+    as the compiled gather, with no index arithmetic -- at several reads in
+    flight per thread, beside the compiled gather itself and the coset and
+    direct affine gathers of the 1000-CNOT circuit."""
+    import torch
+    from paper_quant_ph_0308158_gb300 import Simulator, build, gather_rows, jit_precompile
+
+    build.build()
+    torch.cuda.set_device(local)
+    cfg = workload("mixed_m28")
+    M, steps = cfg["M"], cfg["steps"]
+    n = 1 << M
+    stream = torch.cuda.current_stream()
+    k1 = torch.empty(n, dtype=torch.complex128, pin_memory=True)
+    W.random_state(M, np.complex128, cfg["state_seed"], out=k1.numpy())
+    d_in = k1.to("cuda")
+    d_out = torch.empty_like(d_in)
+    probs = torch.empty(n, dtype=torch.float64, device="cuda")
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    peak, _ = hbm_peak()
+    alg = n * (16 + 16 + 8)
+
+    def timed(fn, k=args.steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    out = {}
+    with Simulator(M, np.complex128) as sim:
+        sim.row_array(steps, rows.data_ptr())
+        sim.synchronize()
+    for U in (4, 8, 16):
+        ms = timed(lambda: gather_rows(d_in.data_ptr(), d_out.data_ptr(), rows.data_ptr(), M,
+                                       np.complex128, probs.data_ptr(), U, stream.cuda_stream))
+        out["rows_U%d" % U] = {"ms": ms, "alg_GBps": alg / ms / 1e6,
+                               "alg_GBps_with_rows": (alg + 8 * n) / ms / 1e6}
+    del rows
+    out["copy_4GiB"] = {"ms": timed(lambda: d_out.copy_(d_in))}
+    out["copy_4GiB"]["GBps"] = 2 * 16 * n / out["copy_4GiB"]["ms"] / 1e6
+    jit_precompile(M, np.complex128, steps, canonicalize=False)
+    cn = workload("cnot_m28")
+    for name, st, jit, coset in (("jit_gather_mix1000", steps, True, True),
+                                 ("coset_gather_cnot1000", cn["steps"], False, True),
+                                 ("affine_gather_cnot1000", cn["steps"], False, False)):
+        with Simulator(M, np.complex128) as sim:
+            sim.set_canonicalize(False)
+            sim.set_jit(jit)
+            sim.set_coset(coset)
+            sim.load_state(k1.numpy())
+            ms = timed(lambda: sim.apply_probabilities(st, probs.data_ptr()))
+        out[name] = {"ms": ms, "alg_GBps": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak}
+    if rank == 0:
+        print(json.dumps({"workload": "gather_floor_M28_c128", "peak_GBps": peak,
+                          "alg_bytes_per_pass": alg, "results": out}), flush=True)
+    return 0
+
+
 def run_parity_scan(args, rank, ws, local):
     """Sec. 4 computational example at every M of a range: the parity program
     on the alternating input (generated on the device from its qubits, App. 1),
@@ -922,7 +990,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
-                             "batch_cnot", "batch_mixed", "serve", "parity_scan"])
+                             "batch_cnot", "batch_mixed", "serve", "parity_scan", "gather_floor"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
     ap.add_argument("--low-bits", type=int, default=0, help="contiguous low tile bits l (0: default)")
@@ -973,6 +1041,8 @@ def main():
         rc = run_batch(args, rank, ws, local)
     elif args.workload == "serve":
         rc = run_serve(args, rank, ws, local) if rank == 0 else 0
+    elif args.workload == "gather_floor":
+        rc = run_gather_floor(args, rank, ws, local) if rank == 0 else 0
     elif args.workload == "parity_scan":
         rc = run_parity_scan(args, rank, ws, local) if rank == 0 else 0
     else:

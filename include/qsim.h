@@ -204,6 +204,21 @@ int qsim_autotune(qsim_ctx *ctx, const qsim_step *steps, size_t L, int reps, qsi
  * controls. */
 int qsim_row_array(qsim_ctx *ctx, const qsim_step *steps, size_t L, uint64_t *d_rows);
 
+/* The paper's final gather for a stored row array (Sec. 2b, k2(i) = k1(x(i)),
+ * with x as qsim_row_array writes it, Sec. 2h): d_out[i] = d_in[d_rows[i] mod
+ * 2^M] for all 2^M rows, and with d_probs non-NULL also d_probs[i] = the FP64
+ * probability of d_out[i] (as qsim_probabilities).  No context: d_in and
+ * d_out (2^M amplitudes of dtype, distinct, aligned to one amplitude), d_rows
+ * (2^M uint64, 8-byte aligned) and d_probs (2^M doubles) are caller-owned
+ * device memory; the work is queued on stream (cudaStream_t, NULL = legacy
+ * default) and the call returns without waiting.  loads_in_flight (0 = 8, or
+ * 4, 8, 16) sets how many source reads each thread keeps in flight.  Rows are
+ * reduced modulo 2^M, so no read leaves d_in.  QSIM_EINVAL for M outside
+ * [1, QSIM_MAX_QUBITS], an unknown dtype, NULL or misaligned pointers,
+ * d_in == d_out or another loads_in_flight. */
+int qsim_gather_rows(const void *d_in, void *d_out, const uint64_t *d_rows, uint32_t M, int dtype,
+                     double *d_probs, int loads_in_flight, void *stream);
+
 /* Force a strategy for subsequent qsim_apply_circuit calls (tests and
  * tuning).  tile_bits: total tile width k (0 = default), low_bits: how many
  * of them are the lowest address bits (0 = default). */
@@ -226,6 +241,14 @@ int qsim_set_jit(qsim_ctx *ctx, int enable);
  * compile_ms (may be NULL) receives the compile time spent by this call. */
 int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L, int canonicalize,
                         double *compile_ms);
+
+/* Affine (NOT/CNOT-only) gather segments, x(i) = A i ^ b over GF(2) (the
+ * Sec. 2h product of such steps): with enable = 1 (default) they run as
+ * coset-blocked tiles, whose reads and writes are aligned runs of 2^run_bits
+ * amplitudes (run_bits 0: runs of 512 bytes; at most 7); with enable = 0 each
+ * output reads its source directly (scattered reads).  Results are identical.
+ * QSIM_EINVAL for run_bits outside [0, 7]. */
+int qsim_set_coset(qsim_ctx *ctx, int enable, int run_bits);
 
 /* Testing hook for failure handling (no counterpart in the paper).  Arms the
  * next tile pass of this context only: its producer warp leaves before

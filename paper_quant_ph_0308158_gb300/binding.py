@@ -34,7 +34,8 @@ QSIM_C128 = 1
 STRATEGY = {"auto": 0, "sweep": 1, "tile": 2, "gather": 3, "inplace": 4}
 PASS_KIND = {1: "sweep", 2: "tile", 3: "gather"}
 KERNEL = {1: "sweep_kernel", 2: "tile_kernel", 3: "gather_affine_kernel",
-          4: "gather_sliced_kernel", 5: "qsim_jit_gather", 6: "probs_kernel"}
+          4: "gather_sliced_kernel", 5: "qsim_jit_gather", 6: "probs_kernel",
+          7: "gather_coset_kernel"}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libqsim.so")
 
@@ -45,7 +46,7 @@ EXPORTS = (
     "qsim_apply_circuit_probabilities", "qsim_apply_circuit_probabilities_async", "qsim_autotune",
     "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
-    "qsim_set_wait_test",
+    "qsim_set_wait_test", "qsim_set_coset", "qsim_gather_rows",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
@@ -152,6 +153,8 @@ def load() -> ctypes.CDLL:
             "qsim_set_profiling": ([p, i], i),
             "qsim_set_jit": ([p, i], i),
             "qsim_set_wait_test": ([p, u32], i),
+            "qsim_set_coset": ([p, i, i], i),
+            "qsim_gather_rows": ([p, p, p, u32, i, p, i, p], i),
             "qsim_jit_precompile": ([u32, i, p, sz, i, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_get_pass_times": ([p, p, p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_get_plan_stats": ([p, ctypes.POINTER(PlanStats)], i),
@@ -350,6 +353,10 @@ class Simulator:
 
     def set_jit(self, enable: bool):
         _check(self._lib.qsim_set_jit(self._ctx, int(bool(enable))))
+
+    def set_coset(self, enable: bool, run_bits: int = 0):
+        """Affine gathers through coset-blocked tiles (default) or direct reads."""
+        _check(self._lib.qsim_set_coset(self._ctx, int(bool(enable)), run_bits))
 
     def set_wait_test(self, poll_limit: int):
         """Arm the next tile pass to give up its pipeline waits (testing)."""
@@ -619,6 +626,15 @@ class Server:
         st = ServerStats()
         _check(self._lib.qsim_server_get_stats(self._s, ctypes.byref(st)))
         return st.as_dict()
+
+
+def gather_rows(d_in: int, d_out: int, d_rows: int, M: int, dtype, d_probs: int = 0,
+                loads_in_flight: int = 0, stream: int = 0):
+    """k2(i) = k1(x(i)) for a stored row array (device pointers, no context)."""
+    L = load()
+    _check(L.qsim_gather_rows(ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), ctypes.c_void_p(d_rows),
+                              M, dtype_code(dtype), ctypes.c_void_p(d_probs or None), loads_in_flight,
+                              ctypes.c_void_p(stream or None)))
 
 
 def version() -> str:

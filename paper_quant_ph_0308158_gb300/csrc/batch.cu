@@ -224,6 +224,7 @@ int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *c
     o.scratch_available = true;
     o.strategy = QSIM_STRATEGY_GATHER;
     o.cancel_adjacent = false;
+    o.coset = false;  // affine passes run inside batch_kernel work items
     for (size_t i = 0; i < n; ++i) {
         std::string msg;
         int rc = make_plan(M[i], steps[i], L[i], o, &b->plans[i], &msg);

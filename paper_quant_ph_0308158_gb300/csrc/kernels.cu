@@ -11,6 +11,8 @@
 //                         (Sec. 2i: sequential steps processed together).
 //   gather_affine_kernel  k2(i) = k1(A i ^ b) for CNOT/NOT segments
 //                         (Sec. 2h product of the steps, Sec. 2b gather).
+//   gather_coset_kernel   the same map over coset tiles of the output space,
+//                         so that reads and writes are aligned runs.
 //   gather_sliced_kernel  k2(i) = k1(x(i)) with x(i) evaluated for 64 output
 //                         indices at once in bit-sliced form, steps applied
 //                         last to first (Sec. 2h product, Sec. 2b gather).
@@ -687,6 +689,197 @@ __global__ void __launch_bounds__(kThreads, 2) row_array_kernel(uint64_t *__rest
                                     cbase, smem, nullptr);
 }
 
+// ============================================================================
+// (c) coset-blocked affine gather: coalesced reads and writes
+// ============================================================================
+
+// A CTA owns groups of 2^e coset tiles (see GatherPass): a producer warp
+// loads each tile's 2^d source runs of 2^r amplitudes with bulk-async copies
+// into one pipeline stage; 16 consumer warps write the tile's 2^d output runs,
+// each output taking its source from the stage through the pass's local
+// permutation (plus the tile's low-bit offset).  Every global access is part
+// of an aligned run of 2^r amplitudes.
+constexpr int kCosetMaxGroup = 64;  // tiles per stage
+
+struct CosetKParams {
+    const char *in;
+    char *out;
+    double *probs;                 // non-null: also write FP64 probabilities
+    int *err;
+    const uint64_t *tabs;          // out-base [ctb][256], source-base [ctb][256], dstrun, srcrun, perm
+    uint64_t n_groups;             // tiles / 2^e
+    uint64_t bvec;
+    uint32_t r, d, e, ctb, stages, wait_limit;
+};
+
+struct CosetStageMeta {
+    uint64_t ob[kCosetMaxGroup];   // output base of each tile
+    uint64_t sb[kCosetMaxGroup];   // source base of each tile (with its low bits)
+    uint32_t end;                  // no more groups
+    uint32_t pad;
+};
+
+template <int B, bool PROBS>
+__global__ void __launch_bounds__(kTileThreads + 32, 1) gather_coset_kernel(CosetKParams p)
+{
+    using A = typename AmpOf<B>::T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t rd = p.r + p.d;
+    const uint32_t G = 1u << p.e;
+    const size_t stage_bytes = (size_t)B << (rd + p.e);
+    const uint32_t nd = 1u << p.d;
+    char *bufs = reinterpret_cast<char *>(smem);
+    CosetStageMeta *meta = reinterpret_cast<CosetStageMeta *>(smem + stage_bytes * p.stages);
+    uint64_t *full = reinterpret_cast<uint64_t *>(meta + p.stages);
+    uint64_t *empty = full + p.stages;
+    uint64_t *dstrun = empty + p.stages;
+    uint64_t *srcrun = dstrun + nd;
+    uint16_t *perm = reinterpret_cast<uint16_t *>(srcrun + nd);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nthreads = kTileThreads + 32;
+    const uint64_t *g_dst = p.tabs + 512 * p.ctb;
+    for (uint32_t i = tid; i < 2 * nd; i += nthreads) dstrun[i] = g_dst[i];  // dstrun, srcrun
+    const uint16_t *g_perm = reinterpret_cast<const uint16_t *>(g_dst + 2 * nd);
+    for (uint32_t i = tid; i < (1u << rd); i += nthreads) perm[i] = g_perm[i];
+    if (tid == 0) {
+        for (uint32_t s = 0; s < p.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTileThreads / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const uint64_t per = (p.n_groups + gridDim.x - 1) / gridDim.x;
+    const uint64_t begin = (uint64_t)blockIdx.x * per;
+    const uint64_t end = begin + per < p.n_groups ? begin + per : p.n_groups;
+    const uint64_t low = (1ull << p.r) - 1ull;
+
+    if (warp == kTileThreads / 32) {
+        // ---------------- producer warp ----------------
+        const uint32_t run_bytes = (uint32_t)B << p.r;
+        const uint64_t *tout = p.tabs, *tsrc = p.tabs + 256 * p.ctb;
+        for (uint32_t it = 0;; ++it) {
+            const uint32_t s = it % p.stages;
+            if (it >= p.stages && !mbar_wait_bounded(&empty[s], ((it / p.stages) - 1) & 1u, p.wait_limit)) {
+                if (lane == 0) atomicOr(p.err, 2);
+                return;
+            }
+            const uint64_t g = begin + it;
+            if (g >= end) {
+                if (lane == 0) {
+                    meta[s].end = 1;
+                    mbar_arrive(&full[s]);  // end marker, no bytes
+                }
+                return;
+            }
+            for (uint32_t q = lane; q < G; q += 32) {
+                const uint64_t t = (g << p.e) | q;
+                uint64_t ob = 0, sb = p.bvec;
+                for (uint32_t k = 0; k < p.ctb; ++k) {
+                    const uint32_t v = (uint32_t)((t >> (8 * k)) & 255u);
+                    ob ^= __ldg(tout + 256 * k + v);
+                    sb ^= __ldg(tsrc + 256 * k + v);
+                }
+                meta[s].ob[q] = ob;
+                meta[s].sb[q] = sb;
+            }
+            if (lane == 0) meta[s].end = 0;
+            __syncwarp();
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)stage_bytes);
+            __syncwarp();
+            char *buf = bufs + stage_bytes * s;
+            for (uint32_t idx = lane; idx < (G << p.d); idx += 32) {
+                const uint32_t q = idx >> p.d, gam = idx & (nd - 1);
+                const uint64_t run = (meta[s].sb[q] & ~low) ^ srcrun[gam];
+                bulk_g2s(buf + (size_t)idx * run_bytes, p.in + run * B, run_bytes, &full[s]);
+            }
+        }
+    }
+
+    // ---------------- consumer warps ----------------
+    A *dst = reinterpret_cast<A *>(p.out);
+    const uint32_t nloc = 1u << rd;
+    const uint32_t total = G << rd;
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t s = it % p.stages;
+        if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u, p.wait_limit)) {
+            if (tid == 0) atomicOr(p.err, 1);
+            return;
+        }
+        if (meta[s].end) break;
+        const A *buf = reinterpret_cast<const A *>(bufs + stage_bytes * s);
+        for (uint32_t j0 = 0; j0 < total; j0 += kTileThreads * 4) {
+            A v[4];
+            uint64_t o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + tid + u * kTileThreads;
+                if (j < total) {
+                    const uint32_t q = j >> rd, jj = j & (nloc - 1);
+                    const uint64_t sb = meta[s].sb[q];
+                    v[u] = buf[((uint32_t)q << rd) | (perm[jj] ^ (uint32_t)(sb & low))];
+                    o[u] = (meta[s].ob[q] ^ dstrun[jj >> p.r]) | (jj & low);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t j = j0 + tid + u * kTileThreads;
+                if (j < total) {
+                    dst[o[u]] = v[u];
+                    if (PROBS) p.probs[o[u]] = amp_prob(v[u]);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+    }
+}
+
+// ============================================================================
+// gather by a stored row array: k2(i) = k1(x(i)) (Sec. 2b), x given
+// ============================================================================
+
+// Each thread keeps U source reads in flight: U coalesced row-array reads,
+// then U reads of single amplitudes at those rows, then U coalesced stores.
+// Rows are taken modulo 2^M.  With the row array of a circuit this is the
+// same random-read pattern as that circuit's gather pass, with no index
+// arithmetic.
+template <int B, int U>
+__global__ void __launch_bounds__(kThreads) gather_rows_kernel(const char *__restrict__ in,
+                                                               char *__restrict__ out,
+                                                               const uint64_t *__restrict__ rows,
+                                                               uint64_t n, double *__restrict__ probs)
+{
+    using A = typename AmpOf<B>::T;
+    const A *src = reinterpret_cast<const A *>(in);
+    A *dst = reinterpret_cast<A *>(out);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += U * stride) {
+        uint64_t x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = i0 + u * stride;
+            x[u] = i < n ? (__ldcs(rows + i) & (n - 1)) : 0;
+        }
+        A v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * stride < n) v[u] = ld_row<true>(&src[x[u]]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = i0 + u * stride;
+            if (i < n) {
+                dst[i] = v[u];
+                if (probs) probs[i] = amp_prob(v[u]);
+            }
+        }
+    }
+}
+
 // Sweep of pair indices [q0, q1) of one step (in place).
 template <int B>
 __device__ __forceinline__ void sweep_range(char *__restrict__ state, const SweepParams &p,
@@ -1019,12 +1212,56 @@ static cudaError_t launch_sliced(const void *in, void *out, uint32_t M, uint64_t
     return cudaGetLastError();
 }
 
+size_t coset_smem_bytes(int amp_bytes, uint32_t r, uint32_t d, uint32_t e, uint32_t *stages)
+{
+    const size_t stage = (size_t)amp_bytes << (r + d + e);
+    const size_t fixed = 2 * sizeof(uint64_t) * ((size_t)1 << d) + sizeof(uint16_t) * ((size_t)1 << (r + d));
+    const size_t per = stage + sizeof(CosetStageMeta) + 2 * sizeof(uint64_t);
+    const size_t budget = 200 * 1024;
+    uint32_t st = (uint32_t)((budget - fixed) / per);
+    st = st > 8 ? 8 : st;
+    if (st < 1) st = 1;
+    if (stages) *stages = st;
+    return per * st + fixed;
+}
+
+static int launch_coset(const void *in, void *out, int amp_bytes, const GatherPass &g,
+                        const uint64_t *d_tables, int *d_err, double *d_probs, cudaStream_t s,
+                        uint32_t wait_limit)
+{
+    CosetKParams p;
+    p.in = static_cast<const char *>(in);
+    p.out = static_cast<char *>(out);
+    p.probs = d_probs;
+    p.err = d_err;
+    p.tabs = d_tables + g.coset_off;
+    p.n_groups = g.n_tiles >> g.ce;
+    p.bvec = g.bvec;
+    p.r = g.cr;
+    p.d = g.cd;
+    p.e = g.ce;
+    p.ctb = g.ctb;
+    p.wait_limit = wait_limit ? wait_limit : kWaitLimit;
+    const size_t smem = coset_smem_bytes(amp_bytes, g.cr, g.cd, g.ce, &p.stages);
+    const uint64_t cap = (uint64_t)num_sms();
+    const int grid = (int)(p.n_groups < cap ? p.n_groups : cap);
+    auto run = [&](auto kernel) -> cudaError_t {
+        cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        kernel<<<grid, kTileThreads + 32, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    if (amp_bytes == 8) return d_probs ? run(gather_coset_kernel<8, true>) : run(gather_coset_kernel<8, false>);
+    return d_probs ? run(gather_coset_kernel<16, true>) : run(gather_coset_kernel<16, false>);
+}
+
 int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &g,
-                  const uint64_t *d_tables, const SlicedStep *d_steps, int * /*d_err*/,
+                  const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err,
                   double *d_probs, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint64_t n = 1ull << M;
+    if (g.affine && g.coset) return launch_coset(in, out, amp_bytes, g, d_tables, d_err, d_probs, s, 0);
     if (g.affine) {
         const uint64_t want = (n + kThreads * 4 - 1) / (kThreads * 4);
         const uint64_t cap = (uint64_t)num_sms() * 8;
@@ -1051,6 +1288,27 @@ int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const Ga
                       : launch_sliced<8, false>(in, out, M, n, st, g.nsteps, d_probs, s);
     return M > 32 ? launch_sliced<16, true>(in, out, M, n, st, g.nsteps, d_probs, s)
                   : launch_sliced<16, false>(in, out, M, n, st, g.nsteps, d_probs, s);
+}
+
+int launch_gather_rows(const void *in, void *out, const uint64_t *rows, int amp_bytes, uint32_t M,
+                       double *d_probs, int loads_in_flight, void *stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t n = 1ull << M;
+    const int U = loads_in_flight;
+    const uint64_t want = (n + (uint64_t)kThreads * U - 1) / ((uint64_t)kThreads * U);
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    const int grid = (int)(want < cap ? (want ? want : 1) : cap);
+    const char *i = static_cast<const char *>(in);
+    char *o = static_cast<char *>(out);
+#define QSIM_ROWS(BB, UU) gather_rows_kernel<BB, UU><<<grid, kThreads, 0, s>>>(i, o, rows, n, d_probs)
+    if (amp_bytes == 8) {
+        if (U == 4) QSIM_ROWS(8, 4); else if (U == 8) QSIM_ROWS(8, 8); else QSIM_ROWS(8, 16);
+    } else {
+        if (U == 4) QSIM_ROWS(16, 4); else if (U == 8) QSIM_ROWS(16, 8); else QSIM_ROWS(16, 16);
+    }
+#undef QSIM_ROWS
+    return cudaGetLastError();
 }
 
 int probabilities_partials_needed() { return kProbBlocks; }

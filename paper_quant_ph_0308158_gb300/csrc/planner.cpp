@@ -395,6 +395,156 @@ void plan_tiles(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> 
 
 bool is_affine_step(const qsim_step &s) { return popcount64(s.ctrl_mask) <= 1; }
 
+// Vectors over GF(2) (bit b = coordinate b) in reduced echelon form: every
+// kept vector has a pivot (its highest set bit) that no other kept vector has.
+struct Echelon {
+    uint64_t v[64];
+    bool has[64] = {false};
+    int rank = 0;
+    // Insert x; returns false when x is already in the span.
+    bool add(uint64_t x)
+    {
+        for (int b = 63; b >= 0; --b)
+            if (has[b] && ((x >> b) & 1ull)) x ^= v[b];
+        if (!x) return false;
+        const int p = 63 - __builtin_clzll(x);
+        for (int b = 0; b < 64; ++b)
+            if (has[b] && ((v[b] >> p) & 1ull)) v[b] ^= x;
+        v[p] = x;
+        has[p] = true;
+        ++rank;
+        return true;
+    }
+};
+
+uint64_t apply_cols(const uint64_t *col, uint64_t i)
+{
+    uint64_t x = 0;
+    for (; i; i &= i - 1) x ^= col[__builtin_ctzll(i)];
+    return x;
+}
+
+// Coset tiles of the affine map x(i) = A i ^ b, A given by its columns
+// col[j] = A e_j (invertible).  Returns false if A is singular (never for a
+// product of NOT/CNOT steps).
+//
+// S = span(e_0..e_{r-1}) + A^-1 span(e_0..e_{r-1}) has a basis of the r low
+// unit vectors and d vectors w_k without low bits, in reduced echelon form
+// with pivots p_k; the other high bits ("complement" bits) number a tile.
+// Output i = T(t) ^ dstrun[beta] ^ l (l < 2^r) for tile t, where T deposits
+// t into the complement bits: a bijection, and each (t, beta) is an aligned
+// run of 2^r outputs.  A S contains the low source bits, so its high parts
+// have a basis u_k (pivots q_k) of the same size d, and the sources of tile t
+// are the aligned runs (A T(t) ^ b) & ~low ^ srcrun[gamma].  The source of
+// local output (beta, l) is y = A(dstrun[beta] ^ l): run gamma (bits q_k of
+// y), offset (y ^ A T(t) ^ b) & low.
+bool emit_coset(uint32_t M, const uint64_t *col, uint64_t bvec, const PlanOptions &o, GatherPass *gp,
+                Plan *plan)
+{
+    const uint32_t amp = (uint32_t)o.amp_bytes;
+    uint32_t r = o.coset_run_bits > 0 ? (uint32_t)o.coset_run_bits : (amp == 16 ? 5u : 6u);
+    r = std::min(std::min(r, 7u), M);  // local indices (r + d <= 14 bits) fit 16 bits
+    if (amp == 8 && r < 1) return false;  // bulk copies move >= 16 bytes
+    const uint64_t low = (1ull << r) - 1ull;
+    // A^-1 by elimination on the columns, remembering which columns combine
+    uint64_t piv_v[64], piv_c[64];
+    bool has[64] = {false};
+    for (uint32_t j = 0; j < M; ++j) {
+        uint64_t v = col[j], c = 1ull << j;
+        for (int b = (int)M - 1; b >= 0 && v; --b) {
+            if (!((v >> b) & 1ull)) continue;
+            if (has[b]) {
+                v ^= piv_v[b];
+                c ^= piv_c[b];
+            } else {
+                piv_v[b] = v;
+                piv_c[b] = c;
+                has[b] = true;
+                v = 0;
+                c = 0;
+                break;
+            }
+        }
+        if (v || c) return false;  // a dependent column
+    }
+    auto solve = [&](uint64_t target) {  // w with A w = target
+        uint64_t w = 0;
+        for (int b = (int)M - 1; b >= 0; --b)
+            if ((target >> b) & 1ull) {
+                target ^= piv_v[b];
+                w ^= piv_c[b];
+            }
+        return w;
+    };
+    Echelon W;
+    for (uint32_t j = 0; j < r; ++j) W.add(solve(1ull << j) & ~low);
+    const uint32_t d = (uint32_t)W.rank;
+    std::vector<uint64_t> wv, pos;  // w_k by ascending pivot; complement bits
+    for (uint32_t b = r; b < M; ++b) {
+        if (W.has[b]) wv.push_back(W.v[b]);
+        else pos.push_back(b);
+    }
+    Echelon U;
+    for (uint32_t j = 0; j < r; ++j) U.add(col[j] & ~low);
+    for (uint64_t w : wv) U.add(apply_cols(col, w) & ~low);
+    if ((uint32_t)U.rank != d) return false;
+    std::vector<uint64_t> uv;
+    std::vector<uint32_t> q;
+    for (uint32_t b = r; b < M; ++b)
+        if (U.has[b]) {
+            uv.push_back(U.v[b]);
+            q.push_back(b);
+        }
+    gp->coset = 1;
+    gp->cr = r;
+    gp->cd = d;
+    const uint32_t nc = (uint32_t)pos.size();  // M - r - d
+    gp->n_tiles = 1ull << nc;
+    gp->ctb = (nc + 7) / 8;
+    // tiles per pipeline stage: stages of at least 16 KiB, at most 64 tiles
+    uint32_t e = 0;
+    while (e < nc && e < 6 && ((uint64_t)amp << (r + d + e)) < 16 * 1024) ++e;
+    gp->ce = e;
+    gp->coset_off = (uint32_t)plan->gather_tables.size();
+    std::vector<uint64_t> &tab = plan->gather_tables;
+    for (uint32_t k = 0; k < gp->ctb; ++k)  // out bases
+        for (uint32_t v = 0; v < 256; ++v) {
+            uint64_t t = 0;
+            for (uint32_t j = 0; j < 8; ++j)
+                if (((v >> j) & 1u) && 8 * k + j < nc) t |= 1ull << pos[8 * k + j];
+            tab.push_back(t);
+        }
+    for (uint32_t k = 0; k < gp->ctb; ++k)  // source bases (without b)
+        for (uint32_t v = 0; v < 256; ++v) tab.push_back(apply_cols(col, tab[gp->coset_off + 256 * k + v]));
+    for (uint32_t beta = 0; beta < (1u << d); ++beta) {
+        uint64_t x = 0;
+        for (uint32_t k = 0; k < d; ++k)
+            if ((beta >> k) & 1u) x ^= wv[k];
+        tab.push_back(x);
+    }
+    const size_t src_off = tab.size();
+    for (uint32_t g = 0; g < (1u << d); ++g) {
+        uint64_t x = 0;
+        for (uint32_t k = 0; k < d; ++k)
+            if ((g >> k) & 1u) x ^= uv[k];
+        tab.push_back(x);
+    }
+    const uint32_t nloc = 1u << (r + d);
+    const size_t perm_off = tab.size();
+    tab.resize(perm_off + (nloc + 3) / 4, 0);
+    for (uint32_t j = 0; j < nloc; ++j) {
+        const uint64_t beta = j >> r, l = j & low;
+        const uint64_t y = apply_cols(col, tab[gp->coset_off + 2 * 256 * gp->ctb + beta] ^ l);
+        uint32_t g = 0;
+        for (uint32_t k = 0; k < d; ++k) g |= (uint32_t)((y >> q[k]) & 1ull) << k;
+        if ((y & ~low) != tab[src_off + g]) return false;  // not in A S: cannot happen
+        const uint64_t loc = ((uint64_t)g << r) | (y & low);
+        tab[perm_off + j / 4] |= loc << (16 * (j % 4));
+    }
+    (void)bvec;
+    return true;
+}
+
 // GF(2) affine map x(i) = A i ^ b of the inverse of a NOT/CNOT segment:
 // x = g_1(g_2(... g_n(i))), built by composing each step onto the outputs of
 // the map so far, last step first.  Stored as per-byte XOR tables.
@@ -440,6 +590,13 @@ void emit_affine(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
     }
     p.nsteps = (uint32_t)seg.size();
     p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+    if (o.coset) {
+        const size_t keep = plan->gather_tables.size();
+        if (!emit_coset(M, col, bvec, o, &gp, plan)) {
+            plan->gather_tables.resize(keep);
+            gp.coset = 0;
+        }
+    }
     plan->passes.push_back(p);
 }
 
@@ -619,7 +776,7 @@ int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<Sl
 uint32_t pass_variant(const Pass &p)
 {
     if (p.kind != kGather) return (uint32_t)p.kind;
-    if (p.gather.affine) return 3;
+    if (p.gather.affine) return p.gather.coset ? 7 : 3;
     return p.gather.jit ? 5 : 4;
 }
 

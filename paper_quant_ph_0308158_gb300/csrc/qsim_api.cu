@@ -346,6 +346,25 @@ int qsim_row_array(qsim_ctx *c, const qsim_step *steps, size_t L, uint64_t *d_ro
     return QSIM_OK;
 }
 
+int qsim_gather_rows(const void *d_in, void *d_out, const uint64_t *d_rows, uint32_t M, int dtype,
+                     double *d_probs, int loads_in_flight, void *stream)
+{
+    if (M < 1 || M > QSIM_MAX_QUBITS) return fail(QSIM_EINVAL, "M out of range");
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    if (!d_in || !d_out || !d_rows) return fail(QSIM_EINVAL, "NULL argument");
+    if (d_in == d_out) return fail(QSIM_EINVAL, "the gather is out of place: d_out must differ from d_in");
+    if ((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & (amp - 1) ||
+        (reinterpret_cast<uintptr_t>(d_rows) & 7u) || (reinterpret_cast<uintptr_t>(d_probs) & 7u))
+        return fail(QSIM_EINVAL, "misaligned device pointer");
+    if (loads_in_flight == 0) loads_in_flight = 8;
+    if (loads_in_flight != 4 && loads_in_flight != 8 && loads_in_flight != 16)
+        return fail(QSIM_EINVAL, "loads_in_flight must be 0, 4, 8 or 16");
+    const int e = launch_gather_rows(d_in, d_out, d_rows, (int)amp, M, d_probs, loads_in_flight, stream);
+    if (e != cudaSuccess) return cuda_fail((cudaError_t)e, "row gather launch");
+    return QSIM_OK;
+}
+
 int qsim_read_state(qsim_ctx *c, void *host, size_t n_amps)
 {
     if (!c || !host) return fail(QSIM_EINVAL, "NULL argument");
@@ -395,6 +414,15 @@ int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L,
         total += ms;
     }
     if (compile_ms) *compile_ms = total;
+    return QSIM_OK;
+}
+
+int qsim_set_coset(qsim_ctx *c, int enable, int run_bits)
+{
+    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
+    if (run_bits < 0 || run_bits > 7) return fail(QSIM_EINVAL, "run_bits must be in [0, 7]");
+    c->opts.coset = enable != 0;
+    c->opts.coset_run_bits = run_bits;
     return QSIM_OK;
 }
 

@@ -99,11 +99,24 @@ struct GatherPass {
     uint32_t step_off;   // general: offset in the SlicedStep buffer
     uint32_t nsteps;     // general: number of steps (applied last to first)
     uint64_t bvec;       // affine: constant term
+    // Coset-blocked affine gather (gather_coset_kernel): the output space is
+    // cut into cosets T(t) + S, S = span(low r bits, A^-1 of the low r bits),
+    // so a tile's 2^(r+d) outputs are 2^d aligned runs of 2^r and its
+    // sources are 2^d aligned runs of 2^r too.  Tables at coset_off in
+    // Plan::gather_tables: out-base [ctb][256], source-base [ctb][256] (tile
+    // index bytes), dstrun [2^d], srcrun [2^d], then the local permutation
+    // (2^(r+d) u16, four per word).
+    uint32_t coset;      // 1: run through gather_coset_kernel
+    uint32_t cr, cd, ce; // run bits r, coset bits d, log2 of tiles per stage
+    uint32_t ctb;        // tile-index bytes of the base tables
+    uint32_t coset_off;
+    uint64_t n_tiles;    // 2^(M - r - d)
 };
 
 enum PassKind : uint32_t { kSweep = 1, kTile = 2, kGather = 3 };
 // Kernel variant reported by tracing: 1 sweep, 2 tile, 3 affine gather,
-// 4 bit-sliced gather, 5 compiled gather.
+// 4 bit-sliced gather, 5 compiled gather, 7 coset-blocked affine gather
+// (6 is the probabilities pass).
 uint32_t pass_variant(const struct Pass &p);
 
 struct Pass {
@@ -124,6 +137,8 @@ struct PlanOptions {
     bool scratch_available = false;
     bool cancel_adjacent = true;
     bool jit = false;        // compile non-affine gather segments (jit.cu)
+    bool coset = true;       // affine segments through coset-blocked tiles
+    int coset_run_bits = 0;  // r of those tiles (0: runs of 512 bytes)
     int jit_min_steps = 32;  // shorter segments use the general kernel
 };
 
@@ -191,6 +206,9 @@ int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const Ga
 int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d_probs,
                          double *d_partials, int n_partials, double *d_norm, void *stream);
 int probabilities_partials_needed();
+// k2(i) = k1(rows[i] mod 2^M) with loads_in_flight (4, 8 or 16) reads per thread.
+int launch_gather_rows(const void *in, void *out, const uint64_t *rows, int amp_bytes, uint32_t M,
+                       double *d_probs, int loads_in_flight, void *stream);
 size_t batch_smem_bytes(uint32_t max_sliced_M);
 int launch_product_state(void *state, int amp_bytes, uint32_t M, const double *d_qubits, void *stream);
 int launch_row_array(uint64_t *d_rows, uint32_t M, const SlicedStep *d_steps, uint32_t nsteps,
@@ -202,6 +220,8 @@ int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<Sl
 int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
                        uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream);
 size_t tile_smem_bytes(int amp_bytes, int k);
+// Shared memory of a coset-gather launch and its pipeline depth.
+size_t coset_smem_bytes(int amp_bytes, uint32_t r, uint32_t d, uint32_t e, uint32_t *stages);
 
 // Compiled gather (jit.cu).  Return QSIM_OK or a QSIM_* error with msg set.
 int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *compile_ms,

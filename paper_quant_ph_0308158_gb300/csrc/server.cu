@@ -570,6 +570,7 @@ int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const 
     o.scratch_available = true;
     o.strategy = QSIM_STRATEGY_GATHER;
     o.cancel_adjacent = false;
+    o.coset = false;  // affine passes run inside batch_kernel work items
     std::string msg;
     int rc = make_plan(M, steps, L, o, &r->plan, &msg);
     if (rc != QSIM_OK) return sfail(rc, msg);

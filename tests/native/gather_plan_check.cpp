@@ -3,6 +3,10 @@
 // for the plans of random circuits, evaluates every pass's encoding on
 // sampled rows the way its kernel does, against the circuit's own steps:
 //   - affine passes: x(i) = b ^ XOR over index bytes of the per-byte tables;
+//   - coset tiles of affine passes: every (tile, run, offset) names an output
+//     row once (all rows are covered for M <= 16), the row's source is where
+//     the coset kernel reads it (source run base, run, offset), and every run
+//     is aligned;
 //   - bit-sliced passes: the step descriptors (target, control planes, the
 //     all-ones plane for absent controls, negated controls, fast/slow path)
 //     applied last to first to a single row;
@@ -57,6 +61,30 @@ uint64_t sliced_apply(const SlicedStep &d, uint32_t M, uint64_t row)
     return row ^ (m << t);
 }
 
+// Where the coset kernel writes local output j of tile t and where it reads
+// its source, from the pass's tables alone.
+struct CosetRow {
+    uint64_t out, src;
+};
+CosetRow coset_row(const Plan &plan, const GatherPass &g, uint64_t t, uint32_t j)
+{
+    const uint64_t *tab = plan.gather_tables.data() + g.coset_off;
+    const uint64_t low = (1ull << g.cr) - 1ull;
+    uint64_t ob = 0, sb = g.bvec;
+    for (uint32_t k = 0; k < g.ctb; ++k) {
+        ob ^= tab[256 * k + ((t >> (8 * k)) & 255u)];
+        sb ^= tab[256 * g.ctb + 256 * k + ((t >> (8 * k)) & 255u)];
+    }
+    const uint64_t *dstrun = tab + 512 * g.ctb;
+    const uint64_t *srcrun = dstrun + (1u << g.cd);
+    const uint64_t *perm = srcrun + (1u << g.cd);
+    const uint32_t loc = (uint32_t)((perm[j / 4] >> (16 * (j % 4))) & 0xffffu);
+    CosetRow r;
+    r.out = (ob ^ dstrun[j >> g.cr]) | (j & low);
+    r.src = ((sb & ~low) ^ srcrun[loc >> g.cr]) | ((loc & low) ^ (sb & low));
+    return r;
+}
+
 uint64_t insert_zero(uint64_t x, uint32_t pos)
 {
     const uint64_t lo = x & ((1ull << pos) - 1ull);
@@ -68,7 +96,7 @@ uint64_t insert_zero(uint64_t x, uint32_t pos)
 int main()
 {
     std::mt19937_64 rng(7741);
-    long rows = 0, affine = 0, sliced = 0, compiled = 0, sweeps = 0;
+    long rows = 0, affine = 0, sliced = 0, compiled = 0, sweeps = 0, cosets = 0;
     for (int trial = 0; trial < 1500; ++trial) {
         const uint32_t M = 2 + (uint32_t)(rng() % 33);  // 2..34
         const size_t L = 1 + rng() % 600;
@@ -96,6 +124,7 @@ int main()
         o.scratch_available = true;
         o.cancel_adjacent = (trial & 4) != 0;
         o.jit = (trial & 8) != 0;
+        o.coset_run_bits = (int)(rng() % 8);  // 0: default
         Plan plan;
         std::string msg;
         if (make_plan(M, st.data(), L, o, &plan, &msg) != QSIM_OK) {
@@ -163,10 +192,39 @@ int main()
                                                       : "bit-sliced descriptors map a row wrongly", M);
                 ++rows;
             }
+            if (g.affine && g.coset) {
+                const uint64_t low = (1ull << g.cr) - 1ull;
+                if (g.cr + g.cd + __builtin_ctzll(g.n_tiles) != M) return fail("coset tile count", M);
+                const uint32_t nloc = 1u << (g.cr + g.cd);
+                const uint64_t *tab = plan.gather_tables.data() + g.coset_off;
+                for (uint32_t b = 0; b < (2u << g.cd); ++b)
+                    if (tab[512 * g.ctb + b] & low) return fail("coset run base not aligned", M);
+                if (M <= 16) {  // the tiles cover every row exactly once
+                    std::vector<char> seen(1ull << M, 0);
+                    for (uint64_t t = 0; t < g.n_tiles; ++t)
+                        for (uint32_t j = 0; j < nloc; ++j) {
+                            const CosetRow cr = coset_row(plan, g, t, j);
+                            if (cr.out > all || seen[cr.out]) return fail("coset tiles overlap", M);
+                            seen[cr.out] = 1;
+                            if (cr.src != source_row(st.data(), plan, first, last, cr.out))
+                                return fail("coset tile reads the wrong source", M);
+                        }
+                } else {
+                    for (int smp = 0; smp < 256; ++smp) {
+                        const uint64_t t = rng() % g.n_tiles;
+                        const uint32_t j = (uint32_t)(rng() % nloc);
+                        const CosetRow cr = coset_row(plan, g, t, j);
+                        if (cr.out > all || cr.src != source_row(st.data(), plan, first, last, cr.out))
+                            return fail("coset tile reads the wrong source", M);
+                    }
+                }
+                ++cosets;
+            }
             if (g.affine) ++affine; else ++sliced;
         }
     }
-    std::printf("ok: %ld affine, %ld bit-sliced, %ld compiled, %ld sweep passes; %ld rows\n", affine,
-                sliced, compiled, sweeps, rows);
+    std::printf("ok: %ld affine (%ld coset-tiled), %ld bit-sliced, %ld compiled, %ld sweep passes; %ld rows\n",
+                affine, cosets, sliced, compiled, sweeps, rows);
+    if (cosets == 0) return fail("no coset-tiled pass was checked", 0);
     return 0;
 }

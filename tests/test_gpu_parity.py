@@ -378,7 +378,8 @@ def test_compiled_gather_bit_exact(dtype, M, L, seed):
 FUSED_CASES = [
     ("tile", False, "mixed", "tile_kernel"),
     ("inplace", False, "mixed", "tile_kernel"),
-    ("gather", False, "cnot", "gather_affine_kernel"),
+    ("gather", False, "cnot", "gather_coset_kernel"),
+    ("gather", "nocoset", "cnot", "gather_affine_kernel"),
     ("gather", False, "mixed", "gather_sliced_kernel"),
     ("gather", True, "mixed", "qsim_jit_gather"),
     ("sweep", False, "mixed", "probs_kernel"),  # a sweep cannot: separate pass
@@ -406,7 +407,8 @@ def test_apply_circuit_probabilities(cuda, dtype, strategy, jit, mix, kernel, M)
     plain = torch.empty(1 << M, dtype=torch.float64, device="cuda")
     with Simulator(M, dtype) as sim:
         sim.set_strategy(strategy)
-        sim.set_jit(jit)
+        sim.set_jit(jit is True)
+        sim.set_coset(jit != "nocoset")
         sim.set_canonicalize(False)
         sim.set_profiling(True)
         sim.load_state(k1)
@@ -487,7 +489,10 @@ def test_wide_indices_m33():
         src = oracle.source_rows(M, steps, rows).astype(np.int64)
         np.testing.assert_array_equal(sim.state_tensor()[ridx].cpu().numpy(), k1[src])
         sim.set_jit(False)
-        sim.apply(cnots)                           # affine gather
+        sim.apply(cnots)                           # coset-blocked affine gather
+        sim.set_coset(False)
+        sim.apply(np.concatenate([cnots[::-1], cnots]))  # identity, direct affine gather
+        sim.set_coset(True)
         sim.synchronize()
         both = np.concatenate([steps, cnots])
         src = oracle.source_rows(M, both, rows).astype(np.int64)
