@@ -79,6 +79,8 @@ def workload(name: str):
         return W.config_cnot(28)
     if name == "adder_m28":  # 2 GiB in-place adder: the small case for tile-kernel captures
         return W.config_adder(13)
+    if name == "hybrid_m28":  # register arithmetic then a CNOT layer: strategies mixed per segment
+        return W.config_hybrid(28)
     if name == "parity_m32":  # Sec. 4 example, input generated on the device (App. 1)
         return W.config_parity(32)
     raise SystemExit("unknown workload " + name)
@@ -551,7 +553,17 @@ def run_ours(args, rank, ws, local):
         r2 = measure_resident(args, c2, strategy_for(wl), args.jit, local, ws, args.steps,
                               args.warmup, sample_clocks=False)
         r2.sim.close()
-        also[wl] = {"workload": c2["name"], "value": r2.value, "unit": UNIT,
+        pure = None
+        if wl == "hybrid_m28":  # the same circuit forced into one strategy
+            pure = {}
+            for strat in ("gather", "inplace"):
+                r3 = measure_resident(args, c2, strat, args.jit, local, ws, max(3, args.steps // 2),
+                                      args.warmup, sample_clocks=False)
+                r3.sim.close()
+                pure[strat] = {"ms_per_step": r3.ms_step, "passes": r3.stats["passes"],
+                               "kernel_ms": r3.kernel_ms}
+        also[wl] = {"workload": c2["name"], "value": r2.value, "unit": UNIT, "pure_plans": pure,
+                    "plan_est_ms": r2.stats["est_ms"], "kernel_launches": r2.kernel_launches,
                     "ms_per_step": r2.ms_step, "M": c2["M"], "L": len(c2["steps"]),
                     "dtype": "c128" if np.dtype(c2["dtype"]) == np.complex128 else "c64",
                     "passes_per_step": r2.stats["passes"], "jit": r2.jit_ms is not None,
@@ -989,7 +1001,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32",
+    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32", "hybrid_m28",
                              "batch_cnot", "batch_mixed", "serve", "parity_scan", "gather_floor"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
@@ -1024,7 +1036,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison of the default run")
-    ap.add_argument("--also", default="mixed_m28",
+    ap.add_argument("--also", default="mixed_m28,cnot_m28,hybrid_m28",
                     help="comma-separated single-circuit workloads also timed on the same line "
                          "(device-resident, no e2e); empty: none")
     ap.add_argument("--batch-compare", type=int, default=4096,

@@ -91,6 +91,8 @@ typedef struct qsim_plan_stats {
     double algorithmic_bytes; /* sum over passes of bytes read + written as the
                                  method requires (untouched tiles/pairs excluded) */
     double full_pass_equiv;   /* algorithmic_bytes / (2 * state bytes)           */
+    double est_ms;            /* the planner's cost-model estimate of the plan's
+                                 device time on GB300 (ms)                        */
 } qsim_plan_stats;
 
 /* ---- context lifetime --------------------------------------------------- */
@@ -504,6 +506,27 @@ void qsim_server_destroy(qsim_server *s);
 int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, int strategy,
                       int tile_bits, int low_bits, int scratch_available, qsim_plan_stats *stats,
                       uint64_t *order, uint64_t *pass_ends, uint32_t *pass_kinds, size_t cap);
+
+/* Planning options for qsim_plan_circuit_ex (the switches a context holds). */
+typedef struct qsim_plan_options {
+    int strategy;          /* qsim_strategy                                       */
+    int tile_bits;         /* as qsim_set_strategy (0: default)                   */
+    int low_bits;
+    int scratch_available; /* nonzero: gather passes allowed                      */
+    int jit;               /* nonzero: compiled gather kernels (qsim_set_jit)     */
+    int coset;             /* nonzero: coset-blocked affine gathers (default on)  */
+    int coset_run_bits;    /* as qsim_set_coset                                   */
+    int canonicalize;      /* nonzero: adjacent equal steps cancel (default on)   */
+} qsim_plan_options;
+
+/* qsim_plan_circuit with every planning switch, reporting per pass the kernel
+ * variant (as qsim_get_pass_times: 1 sweep, 2 tile, 3 affine gather, 4
+ * bit-sliced gather, 5 compiled gather, 7 coset gather) and the cost model's
+ * estimated time in ms (pass_est_ms, may be NULL).  opts NULL: defaults. */
+int qsim_plan_circuit_ex(uint32_t M, int dtype, const qsim_step *steps, size_t L,
+                         const qsim_plan_options *opts, qsim_plan_stats *stats, uint64_t *order,
+                         uint64_t *pass_ends, uint32_t *pass_variants, double *pass_est_ms,
+                         size_t cap);
 
 /* ---- allocation-free variant (the paper has no counterpart) --------------- */
 

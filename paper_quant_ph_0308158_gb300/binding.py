@@ -46,7 +46,7 @@ EXPORTS = (
     "qsim_apply_circuit_probabilities", "qsim_apply_circuit_probabilities_async", "qsim_autotune",
     "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
-    "qsim_set_wait_test", "qsim_set_coset", "qsim_gather_rows",
+    "qsim_set_wait_test", "qsim_set_coset", "qsim_gather_rows", "qsim_plan_circuit_ex",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
@@ -71,10 +71,17 @@ class PlanStats(ctypes.Structure):
     _fields_ = [("steps_in", ctypes.c_uint64), ("steps_cancelled", ctypes.c_uint64),
                 ("passes", ctypes.c_uint64), ("sweep_passes", ctypes.c_uint64),
                 ("tile_passes", ctypes.c_uint64), ("gather_passes", ctypes.c_uint64),
-                ("algorithmic_bytes", ctypes.c_double), ("full_pass_equiv", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_double), ("full_pass_equiv", ctypes.c_double),
+                ("est_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int), ("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int),
+                ("scratch_available", ctypes.c_int), ("jit", ctypes.c_int), ("coset", ctypes.c_int),
+                ("coset_run_bits", ctypes.c_int), ("canonicalize", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):
@@ -155,6 +162,8 @@ def load() -> ctypes.CDLL:
             "qsim_set_wait_test": ([p, u32], i),
             "qsim_set_coset": ([p, i, i], i),
             "qsim_gather_rows": ([p, p, p, u32, i, p, i, p], i),
+            "qsim_plan_circuit_ex": ([u32, i, p, sz, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanStats),
+                                      p, p, p, p, sz], i),
             "qsim_jit_precompile": ([u32, i, p, sz, i, ctypes.POINTER(ctypes.c_double)], i),
             "qsim_get_pass_times": ([p, p, p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_get_plan_stats": ([p, ctypes.POINTER(PlanStats)], i),
@@ -244,6 +253,32 @@ def plan_circuit(M: int, dtype, steps, strategy: str = "auto", tile_bits: int = 
     n_ord = int(st.steps_in - st.steps_cancelled)
     return dict(stats=st.as_dict(), order=order[:n_ord].copy(), pass_ends=ends[:n_pass].copy(),
                 kinds=[PASS_KIND[int(k)] for k in kinds[:n_pass]])
+
+
+VARIANT = {1: "sweep", 2: "tile", 3: "affine", 4: "sliced", 5: "compiled", 7: "coset"}
+
+
+def plan_circuit_ex(M: int, dtype, steps, strategy: str = "auto", tile_bits: int = 0,
+                    low_bits: int = 0, scratch: bool = True, jit: bool = False, coset: bool = True,
+                    coset_run_bits: int = 0, canonicalize: bool = True) -> dict:
+    """Host-only planning with every switch: per pass its kernel variant and
+    the cost model's estimated time (ms)."""
+    L = load()
+    s = as_steps(steps)
+    cap = max(len(s), 1)
+    order = np.zeros(cap, dtype=np.uint64)
+    ends = np.zeros(cap, dtype=np.uint64)
+    var = np.zeros(cap, dtype=np.uint32)
+    est = np.zeros(cap, dtype=np.float64)
+    st = PlanStats()
+    o = PlanOptions(STRATEGY[strategy], tile_bits, low_bits, int(scratch), int(jit), int(coset),
+                    coset_run_bits, int(canonicalize))
+    _check(L.qsim_plan_circuit_ex(M, dtype_code(dtype), _ptr(s), len(s), ctypes.byref(o),
+                                  ctypes.byref(st), _ptr(order), _ptr(ends), _ptr(var), _ptr(est), cap))
+    n_pass = int(st.passes)
+    n_ord = int(st.steps_in - st.steps_cancelled)
+    return dict(stats=st.as_dict(), order=order[:n_ord].copy(), pass_ends=ends[:n_pass].copy(),
+                variants=[VARIANT[int(k)] for k in var[:n_pass]], est_ms=est[:n_pass].copy())
 
 
 class Simulator:

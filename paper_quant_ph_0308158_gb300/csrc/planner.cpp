@@ -438,12 +438,31 @@ uint64_t apply_cols(const uint64_t *col, uint64_t i)
 // are the aligned runs (A T(t) ^ b) & ~low ^ srcrun[gamma].  The source of
 // local output (beta, l) is y = A(dstrun[beta] ^ l): run gamma (bits q_k of
 // y), offset (y ^ A T(t) ^ b) & low.
+bool emit_coset_r(uint32_t M, const uint64_t *col, uint32_t r, const PlanOptions &o, GatherPass *gp,
+                  Plan *plan);
+
+// Largest run length r (at most the requested one) whose tiles of 2^(r+d)
+// amplitudes stay within 64 KiB, so that the pipeline holds two stages.
 bool emit_coset(uint32_t M, const uint64_t *col, uint64_t bvec, const PlanOptions &o, GatherPass *gp,
                 Plan *plan)
 {
+    (void)bvec;
     const uint32_t amp = (uint32_t)o.amp_bytes;
     uint32_t r = o.coset_run_bits > 0 ? (uint32_t)o.coset_run_bits : (amp == 16 ? 5u : 6u);
     r = std::min(std::min(r, 7u), M);  // local indices (r + d <= 14 bits) fit 16 bits
+    const size_t keep = plan->gather_tables.size();
+    for (; r >= 1; --r) {
+        if (!emit_coset_r(M, col, r, o, gp, plan)) return false;
+        if (((uint64_t)amp << (gp->cr + gp->cd)) <= 64 * 1024) return true;
+        plan->gather_tables.resize(keep);
+    }
+    return false;
+}
+
+bool emit_coset_r(uint32_t M, const uint64_t *col, uint32_t r, const PlanOptions &o, GatherPass *gp,
+                  Plan *plan)
+{
+    const uint32_t amp = (uint32_t)o.amp_bytes;
     if (amp == 8 && r < 1) return false;  // bulk copies move >= 16 bytes
     const uint64_t low = (1ull << r) - 1ull;
     // A^-1 by elimination on the columns, remembering which columns combine
@@ -541,7 +560,6 @@ bool emit_coset(uint32_t M, const uint64_t *col, uint64_t bvec, const PlanOption
         const uint64_t loc = ((uint64_t)g << r) | (y & low);
         tab[perm_off + j / 4] |= loc << (16 * (j % 4));
     }
-    (void)bvec;
     return true;
 }
 
@@ -684,6 +702,149 @@ void plan_gather(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
     }
 }
 
+// ---- cost model ---------------------------------------------------------------
+//
+// Estimated device time of a pass on GB300, from measured rates (6.78 TB/s
+// copy bandwidth): tile and sweep passes stream their bytes at about 90 %
+// and 87 % of it; a coset gather streams aligned runs; a gather that reads
+// single amplitudes at scattered rows pays a 64-byte DRAM access per read and
+// runs those at about half the copy rate; evaluating a non-affine segment
+// costs integer work per step and output (bit-sliced interpreter or compiled
+// kernel); every launch costs a few microseconds.
+constexpr double kPeakBytesPerS = 6.78e12;
+constexpr double kEffTile = 0.90;
+constexpr double kEffSweep = 0.87;
+constexpr double kEffCoset = 0.80;
+constexpr double kRandomReadBytes = 64.0;
+constexpr double kEffRandom = 0.50;
+constexpr double kSlicedStepS = 2.8e-14;  // per step and output, interpreter
+constexpr double kCompiledStepS = 2.2e-15; // per step and output, compiled kernel
+constexpr double kLaunchS = 4e-6;
+
+double gather_cost_s(uint32_t M, size_t amp, bool affine, bool coset, bool compiled, size_t nsteps)
+{
+    const double n = (double)(1ull << M);
+    if (affine && coset) return kLaunchS + 2.0 * n * (double)amp / (kEffCoset * kPeakBytesPerS);
+    double t = kLaunchS + n * (kRandomReadBytes + (double)amp) / (kEffRandom * kPeakBytesPerS);
+    if (!affine) t += (double)nsteps * n * (compiled ? kCompiledStepS : kSlicedStepS);
+    return t;
+}
+
+double pass_cost_s(const Pass &p, uint32_t M, size_t amp)
+{
+    if (p.kind == kSweep) return kLaunchS + p.alg_bytes / (kEffSweep * kPeakBytesPerS);
+    if (p.kind == kTile) return kLaunchS + p.alg_bytes / (kEffTile * kPeakBytesPerS);
+    const GatherPass &g = p.gather;
+    return gather_cost_s(M, amp, g.affine != 0, g.coset != 0, g.jit != 0,
+                         g.jit ? g.jit_n : g.nsteps);
+}
+
+double plan_cost_s(const Plan &plan, uint32_t M, size_t amp)
+{
+    double t = 0;
+    for (const Pass &p : plan.passes) t += pass_cost_s(p, M, amp);
+    return t;
+}
+
+// Estimated cost of one gather pass (or several, beyond the step limit) over
+// order[i, j), as plan_gather would cut it.
+double gather_range_cost_s(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &order,
+                           size_t i, size_t j, const PlanOptions &o)
+{
+    double t = 0;
+    while (i < j) {
+        const size_t e = std::min(j, i + (size_t)kMaxGatherSteps);
+        bool affine = true, wide = false;
+        for (size_t q = i; q < e; ++q) {
+            affine = affine && is_affine_step(steps[order[q]]);
+            wide = wide || popcount64(steps[order[q]].ctrl_mask) > kSlicedMaxControls;
+        }
+        if (wide) return 1e30;  // left to the pure plans
+        const bool compiled = !affine && o.jit && M >= 10 && (int)(e - i) >= o.jit_min_steps;
+        t += gather_cost_s(M, o.amp_bytes, affine, o.coset, compiled, e - i);
+        i = e;
+    }
+    return t;
+}
+
+// Per-segment choice (Sec. 2i groups sequential steps; each group may take
+// its own strategy).  The applied order is cut at long NOT/CNOT runs, which a
+// coset gather moves in one streaming pass; each run of blocks between cuts
+// becomes either one gather (its steps merged) or the tile passes of its
+// blocks, whichever the cost model prefers, by dynamic programming over the
+// blocks.  Returns false when there is nothing to cut.
+constexpr size_t kMinAffineRun = 24;
+constexpr size_t kMaxBlocks = 48;
+
+bool plan_hybrid(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &order,
+                 const PlanOptions &o, Plan *plan)
+{
+    // blocks: [start, end) of order; affine runs of >= kMinAffineRun steps
+    // stand alone, everything between them forms one block
+    std::vector<std::pair<size_t, size_t>> blocks;
+    const size_t n = order.size();
+    size_t cur = 0, i = 0;
+    while (i < n) {
+        if (!is_affine_step(steps[order[i]])) {
+            ++i;
+            continue;
+        }
+        size_t j = i;
+        while (j < n && is_affine_step(steps[order[j]])) ++j;
+        if (j - i >= kMinAffineRun) {
+            if (cur < i) blocks.push_back({cur, i});
+            blocks.push_back({i, j});
+            cur = j;
+        }
+        i = j;
+    }
+    if (cur < n) blocks.push_back({cur, n});
+    if (blocks.size() < 2 || blocks.size() > kMaxBlocks) return false;
+    const size_t B = blocks.size();
+    // tile cost of each block alone (its own greedy segmentation)
+    std::vector<double> tcost(B);
+    for (size_t b = 0; b < B; ++b) {
+        Plan tmp;
+        std::vector<uint64_t> sub(order.begin() + blocks[b].first, order.begin() + blocks[b].second);
+        plan_tiles(M, steps, sub, o, true, &tmp);
+        tcost[b] = plan_cost_s(tmp, M, o.amp_bytes);
+    }
+    // best[j]: cheapest cover of blocks [0, j); choice: start block and kind
+    std::vector<double> best(B + 1, 1e300);
+    std::vector<size_t> from(B + 1, 0);
+    std::vector<char> as_gather(B + 1, 0);
+    best[0] = 0;
+    for (size_t j = 1; j <= B; ++j) {
+        double tiles = 0;
+        for (size_t a = j; a-- > 0;) {
+            tiles += tcost[a];
+            const double g = gather_range_cost_s(M, steps, order, blocks[a].first, blocks[j - 1].second, o);
+            const double c = std::min(tiles, g);
+            if (best[a] + c < best[j]) {
+                best[j] = best[a] + c;
+                from[j] = a;
+                as_gather[j] = g < tiles;
+            }
+        }
+    }
+    std::vector<std::pair<size_t, size_t>> segs;  // (block range end j, start a)
+    for (size_t j = B; j > 0; j = from[j]) segs.push_back({j, from[j]});
+    std::reverse(segs.begin(), segs.end());
+    for (const auto &sg : segs) {
+        const size_t a = sg.second, j = sg.first;
+        if (as_gather[j]) {
+            std::vector<uint64_t> sub(order.begin() + blocks[a].first, order.begin() + blocks[j - 1].second);
+            plan_gather(M, steps, sub, o, plan);
+        } else {
+            for (size_t b = a; b < j; ++b) {
+                std::vector<uint64_t> sub(order.begin() + blocks[b].first, order.begin() + blocks[b].second);
+                plan_tiles(M, steps, sub, o, true, plan);
+            }
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o, Plan *plan,
@@ -726,24 +887,28 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
         plan_gather(M, steps, order, oo, plan);
         return QSIM_OK;
     }
-    // AUTO: in-place tile/sweep plan, replaced by gather passes when a
-    // scratch buffer is allowed and the gather plan moves fewer bytes.
+    // AUTO: the in-place tile/sweep plan, or -- when a scratch buffer is
+    // allowed -- the gather plan or a per-segment mix of both, whichever the
+    // cost model expects to run fastest.
     Plan tp;
     tp.steps_in = plan->steps_in;
     tp.cancelled = plan->cancelled;
     plan_tiles(M, steps, order, oo, true, &tp);
+    const double tcost = plan_cost_s(tp, M, oo.amp_bytes);
     if (oo.scratch_available) {
         Plan gp;
         gp.steps_in = plan->steps_in;
         gp.cancelled = plan->cancelled;
         plan_gather(M, steps, order, oo, &gp);
-        // A gather pass reads scattered amplitudes: charge the sector
-        // over-fetch (32-byte sectors) on its reads.
-        const double over = std::max(1.0, 32.0 / (double)oo.amp_bytes);
-        double tcost = 0, gcost = 0;
-        for (const Pass &p : tp.passes) tcost += p.alg_bytes;
-        for (const Pass &p : gp.passes)
-            gcost += p.kind == kGather ? p.alg_bytes * (over + 1.0) / 2.0 : p.alg_bytes;
+        const double gcost = plan_cost_s(gp, M, oo.amp_bytes);
+        Plan hp;
+        hp.steps_in = plan->steps_in;
+        hp.cancelled = plan->cancelled;
+        const double hcost = plan_hybrid(M, steps, order, oo, &hp) ? plan_cost_s(hp, M, oo.amp_bytes) : 1e300;
+        if (hcost < gcost && hcost < tcost) {
+            *plan = std::move(hp);
+            return QSIM_OK;
+        }
         if (gcost < tcost) {
             *plan = std::move(gp);
             return QSIM_OK;
@@ -752,6 +917,10 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
     *plan = std::move(tp);
     return QSIM_OK;
 }
+
+double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp) { return 1e3 * plan_cost_s(plan, M, amp); }
+
+double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp) { return 1e3 * pass_cost_s(p, M, amp); }
 
 int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<SlicedStep> *out,
                     std::string *msg)

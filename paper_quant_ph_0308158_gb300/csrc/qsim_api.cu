@@ -193,6 +193,7 @@ void fill_stats(const Plan &plan, uint32_t M, size_t amp, qsim_plan_stats *st)
         st->algorithmic_bytes += p.alg_bytes;
     }
     st->full_pass_equiv = st->algorithmic_bytes / (2.0 * (double)amp * (double)(1ull << M));
+    st->est_ms = plan_estimated_ms(plan, M, amp);
 }
 
 int plan_options(int strategy, int tile_bits, int low_bits, PlanOptions *o)
@@ -914,6 +915,45 @@ int qsim_plan_circuit(uint32_t M, int dtype, const qsim_step *steps, size_t L, i
     if (pass_ends) std::memcpy(pass_ends, plan.pass_ends.data(), plan.pass_ends.size() * sizeof(uint64_t));
     if (pass_kinds)
         for (size_t i = 0; i < plan.passes.size(); ++i) pass_kinds[i] = (uint32_t)plan.passes[i].kind;
+    return QSIM_OK;
+}
+
+int qsim_plan_circuit_ex(uint32_t M, int dtype, const qsim_step *steps, size_t L,
+                         const qsim_plan_options *opts, qsim_plan_stats *stats, uint64_t *order,
+                         uint64_t *pass_ends, uint32_t *pass_variants, double *pass_est_ms, size_t cap)
+{
+    const size_t amp = amp_bytes_of(dtype);
+    if (!amp) return fail(QSIM_EINVAL, "unknown dtype");
+    qsim_plan_options d{};
+    d.strategy = QSIM_STRATEGY_AUTO;
+    d.scratch_available = 1;
+    d.coset = 1;
+    d.canonicalize = 1;
+    const qsim_plan_options &q = opts ? *opts : d;
+    PlanOptions o;
+    int rc = plan_options(q.strategy, q.tile_bits, q.low_bits, &o);
+    if (rc != QSIM_OK) return rc;
+    if (q.coset_run_bits < 0 || q.coset_run_bits > 7) return fail(QSIM_EINVAL, "coset_run_bits must be in [0, 7]");
+    o.amp_bytes = amp;
+    o.scratch_available = q.scratch_available != 0;
+    o.jit = q.jit != 0;
+    o.coset = q.coset != 0;
+    o.coset_run_bits = q.coset_run_bits;
+    o.cancel_adjacent = q.canonicalize != 0;
+    Plan plan;
+    std::string msg;
+    rc = make_plan(M, steps, L, o, &plan, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    if (stats) fill_stats(plan, M, amp, stats);
+    if ((order && plan.order.size() > cap) ||
+        ((pass_ends || pass_variants || pass_est_ms) && plan.passes.size() > cap))
+        return fail(QSIM_EINVAL, "output capacity too small");
+    if (order) std::memcpy(order, plan.order.data(), plan.order.size() * sizeof(uint64_t));
+    if (pass_ends) std::memcpy(pass_ends, plan.pass_ends.data(), plan.pass_ends.size() * sizeof(uint64_t));
+    for (size_t i = 0; i < plan.passes.size(); ++i) {
+        if (pass_variants) pass_variants[i] = pass_variant(plan.passes[i]);
+        if (pass_est_ms) pass_est_ms[i] = pass_estimated_ms(plan.passes[i], M, amp);
+    }
     return QSIM_OK;
 }
 

@@ -158,6 +158,9 @@ struct Plan {
 int validate_steps(uint32_t M, const qsim_step *steps, size_t L, std::string *msg);
 int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &opt,
               Plan *plan, std::string *msg);
+// The cost model's estimated device time of a plan / one pass (planner.cpp).
+double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp);
+double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp);
 
 // One circuit's pass inside a batched launch (batch.cu builds them).
 struct BatchPass {

@@ -180,6 +180,28 @@ def mixed_circuit(M: int, L: int, seed: int) -> np.ndarray:
     return a
 
 
+def local_mixed_circuit(M: int, L: int, seed: int, target_bits: int = 12) -> np.ndarray:
+    """The mixed gate set (10% NOT, 50% CNOT, 30% Toffoli, 10% NOT with 3-5
+    controls) with every target among the lowest ``target_bits`` address
+    bits and the controls anywhere: arithmetic on a low register."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kinds = rng.choice(4, size=L, p=[0.1, 0.5, 0.3, 0.1])
+    many = rng.integers(3, 6, size=L)
+    nc = np.choose(kinds, [np.zeros(L, np.int64), np.ones(L, np.int64),
+                           np.full(L, 2, np.int64), many])
+    nc = np.minimum(nc, M - 1)
+    tgt = rng.integers(0, target_bits, size=L)
+    keys = rng.random((L, M))
+    keys[np.arange(L), tgt] = 2.0  # the target is never a control
+    ctl = np.argsort(keys, axis=1)[:, :5]
+    a = np.zeros(L, dtype=STEP_DTYPE)
+    a["target"] = tgt
+    m = _masks(ctl, nc)
+    a["ctrl_mask"] = m
+    a["ctrl_pol"] = m
+    return a
+
+
 def random_circuit(M: int, L: int, seed: int, max_controls: int = 4,
                    polarity: bool = True) -> np.ndarray:
     """General random steps for property tests: 0..max_controls controls,
@@ -291,6 +313,17 @@ def config_mixed(M: int = 28, seed: int = 2, L: int = 1000, dtype=np.complex128)
     tag = "c128" if np.dtype(dtype) == np.complex128 else "c64"
     return dict(name="M%d_%s_mix%d" % (M, tag, L), M=M, dtype=dtype,
                 steps=mixed_circuit(M, L, seed), state_seed=seed)
+
+
+def config_hybrid(M: int = 28, seed: int = 6, dtype=np.complex128):
+    """A circuit whose best plan mixes strategies per segment: 300 steps of
+    the mixed gate set on a 12-bit low register (controls anywhere; tile
+    passes keep them local), then a linear layer of 1000 random CNOTs over
+    all bits (one coset gather)."""
+    tag = "c128" if np.dtype(dtype) == np.complex128 else "c64"
+    steps = np.concatenate([local_mixed_circuit(M, 300, seed, 12), cnot_circuit(M, 1000, seed + 1)])
+    return dict(name="M%d_%s_hybrid300x1000" % (M, tag), M=M, dtype=dtype, steps=steps,
+                state_seed=seed)
 
 
 def config_mixed_m28(seed: int = 2, L: int = 1000):

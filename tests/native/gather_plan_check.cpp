@@ -194,6 +194,7 @@ int main()
             }
             if (g.affine && g.coset) {
                 const uint64_t low = (1ull << g.cr) - 1ull;
+                if (((uint64_t)o.amp_bytes << (g.cr + g.cd)) > 64 * 1024) return fail("coset tile above 64 KiB", M);
                 if (g.cr + g.cd + __builtin_ctzll(g.n_tiles) != M) return fail("coset tile count", M);
                 const uint32_t nloc = 1u << (g.cr + g.cd);
                 const uint64_t *tab = plan.gather_tables.data() + g.coset_off;

@@ -316,6 +316,33 @@ def test_adder_m32_workload_sampled():
     assert set(kernels) <= {"tile_kernel", "sweep_kernel"} and kernels[-1] == "tile_kernel"
 
 
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_hybrid_plan_full_state(dtype):
+    """A plan that mixes strategies per segment (tile passes, then a coset
+    gather): every amplitude against the oracle."""
+    cfg = W.config_hybrid(18, dtype=dtype)
+    M, steps = cfg["M"], cfg["steps"]
+    k1 = W.random_state(M, dtype, cfg["state_seed"])
+    want = oracle.apply_circuit(M, k1, steps).astype(dtype)
+    with Simulator(M, dtype) as sim:
+        sim.set_canonicalize(False)
+        sim.set_profiling(True)
+        sim.load_state(k1)
+        sim.apply(steps)
+        got = sim.read_state()
+        kernels = [k for k, _, _ in sim.pass_times()]
+    np.testing.assert_array_equal(got, want)
+    assert "tile_kernel" in kernels and kernels[-1] == "gather_coset_kernel"
+
+
+def test_hybrid_m28_workload_sampled():
+    """The M=28 complex128 hybrid workload as benchmarked (tile passes on the
+    register, one coset gather writing the probabilities)."""
+    st, kernels = _sampled_check(W.config_hybrid(), "auto", jit=True, probs=True)
+    assert st["tile_passes"] >= 1 and st["gather_passes"] == 1
+    assert kernels[-1] == "gather_coset_kernel" and "tile_kernel" in kernels
+
+
 def test_sec4_parity_m32_from_qubits_with_probabilities(cuda):
     """The Sec. 4 example at M = 32 as the benchmark runs it: the alternating
     input generated from its qubits (App. 1), the parity program in place,
