@@ -277,7 +277,8 @@ int qsim_get_plan_stats(qsim_ctx *ctx, qsim_plan_stats *out);
  * for queued work and writes, for each recorded pass (at most cap), the
  * device time in milliseconds, the kernel (1 sweep, 2 tile, 3 affine gather,
  * 4 bit-sliced gather, 5 compiled gather, 6 probabilities from
- * qsim_probabilities_device) and its algorithmic bytes (any pointer may be
+ * qsim_probabilities_device, 7 coset gather, 8 closed tile pass) and its
+ * algorithmic bytes (any pointer may be
  * NULL); *n_out receives the number of recorded launches.  When cap covers
  * them all the record is cleared. */
 int qsim_set_profiling(qsim_ctx *ctx, int enable);
@@ -517,11 +518,17 @@ typedef struct qsim_plan_options {
     int coset;             /* nonzero: coset-blocked affine gathers (default on)  */
     int coset_run_bits;    /* as qsim_set_coset                                   */
     int canonicalize;      /* nonzero: adjacent equal steps cancel (default on)   */
+    int closed_known;      /* nonzero: closed_delta is given                      */
+    uint64_t closed_delta; /* address bits the circuit's net row map can change
+                              (OR over all rows of x(i) ^ i; a context finds it
+                              on the device when compiled kernels are on): with
+                              jit, a closed tile pass is weighed               */
 } qsim_plan_options;
 
 /* qsim_plan_circuit with every planning switch, reporting per pass the kernel
  * variant (as qsim_get_pass_times: 1 sweep, 2 tile, 3 affine gather, 4
- * bit-sliced gather, 5 compiled gather, 7 coset gather) and the cost model's
+ * bit-sliced gather, 5 compiled gather, 7 coset gather, 8 closed tile pass)
+ * and the cost model's
  * estimated time in ms (pass_est_ms, may be NULL).  opts NULL: defaults. */
 int qsim_plan_circuit_ex(uint32_t M, int dtype, const qsim_step *steps, size_t L,
                          const qsim_plan_options *opts, qsim_plan_stats *stats, uint64_t *order,

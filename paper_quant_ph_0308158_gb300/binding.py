@@ -35,7 +35,7 @@ STRATEGY = {"auto": 0, "sweep": 1, "tile": 2, "gather": 3, "inplace": 4}
 PASS_KIND = {1: "sweep", 2: "tile", 3: "gather"}
 KERNEL = {1: "sweep_kernel", 2: "tile_kernel", 3: "gather_affine_kernel",
           4: "gather_sliced_kernel", 5: "qsim_jit_gather", 6: "probs_kernel",
-          7: "gather_coset_kernel"}
+          7: "gather_coset_kernel", 8: "qsim_jit_closed"}
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libqsim.so")
 
@@ -81,7 +81,8 @@ class PlanStats(ctypes.Structure):
 class PlanOptions(ctypes.Structure):
     _fields_ = [("strategy", ctypes.c_int), ("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int),
                 ("scratch_available", ctypes.c_int), ("jit", ctypes.c_int), ("coset", ctypes.c_int),
-                ("coset_run_bits", ctypes.c_int), ("canonicalize", ctypes.c_int)]
+                ("coset_run_bits", ctypes.c_int), ("canonicalize", ctypes.c_int),
+                ("closed_known", ctypes.c_int), ("closed_delta", ctypes.c_uint64)]
 
 
 class BatchStats(ctypes.Structure):
@@ -255,12 +256,13 @@ def plan_circuit(M: int, dtype, steps, strategy: str = "auto", tile_bits: int = 
                 kinds=[PASS_KIND[int(k)] for k in kinds[:n_pass]])
 
 
-VARIANT = {1: "sweep", 2: "tile", 3: "affine", 4: "sliced", 5: "compiled", 7: "coset"}
+VARIANT = {1: "sweep", 2: "tile", 3: "affine", 4: "sliced", 5: "compiled", 7: "coset", 8: "closed"}
 
 
 def plan_circuit_ex(M: int, dtype, steps, strategy: str = "auto", tile_bits: int = 0,
                     low_bits: int = 0, scratch: bool = True, jit: bool = False, coset: bool = True,
-                    coset_run_bits: int = 0, canonicalize: bool = True) -> dict:
+                    coset_run_bits: int = 0, canonicalize: bool = True,
+                    closed_delta: int | None = None) -> dict:
     """Host-only planning with every switch: per pass its kernel variant and
     the cost model's estimated time (ms)."""
     L = load()
@@ -272,7 +274,8 @@ def plan_circuit_ex(M: int, dtype, steps, strategy: str = "auto", tile_bits: int
     est = np.zeros(cap, dtype=np.float64)
     st = PlanStats()
     o = PlanOptions(STRATEGY[strategy], tile_bits, low_bits, int(scratch), int(jit), int(coset),
-                    coset_run_bits, int(canonicalize))
+                    coset_run_bits, int(canonicalize), int(closed_delta is not None),
+                    int(closed_delta or 0))
     _check(L.qsim_plan_circuit_ex(M, dtype_code(dtype), _ptr(s), len(s), ctypes.byref(o),
                                   ctypes.byref(st), _ptr(order), _ptr(ends), _ptr(var), _ptr(est), cap))
     n_pass = int(st.passes)

@@ -114,6 +114,67 @@ uint64_t fnv1a(const std::vector<uint64_t> &k)
     return h;
 }
 
+// The steps as bit-plane updates on planes p0..p{M-1}, last step first (the
+// inverse circuit evaluated on output indices): a NOT complements its target
+// plane, a controlled step XORs the AND of its control planes (a control on
+// |0> complemented) into the target plane.
+void step_lines(std::ostringstream &s, const qsim_step *steps, size_t n)
+{
+    for (size_t q = n; q-- > 0;) {
+        const qsim_step &st = steps[q];
+        s << "    p" << st.target;
+        if (st.ctrl_mask == 0) {
+            s << " = ~p" << st.target << ";\n";
+            continue;
+        }
+        s << " ^= ";
+        bool first = true;
+        for (uint64_t m = st.ctrl_mask; m; m &= m - 1) {
+            const uint32_t b = (uint32_t)__builtin_ctzll(m);
+            if (!first) s << " & ";
+            first = false;
+            s << (((st.ctrl_pol >> b) & 1ull) ? "p" : "~p") << b;
+        }
+        s << ";\n";
+    }
+}
+
+const char *kLanePattern[5] = {"0xaaaaaaaau", "0xccccccccu", "0xf0f0f0f0u", "0xff00ff00u", "0xffff0000u"};
+
+// Source of the kernel that finds which address bits a step list can change:
+// every output row's source x(i) is evaluated (32 rows per thread, bit
+// planes) and the OR over all rows of x(i) ^ i is accumulated into *out.
+std::string generate_delta_source(uint32_t M, const qsim_step *steps, size_t n)
+{
+    std::ostringstream s;
+    s << "typedef unsigned int u32;\ntypedef unsigned long long u64;\n"
+         "extern \"C\" __global__ void __launch_bounds__(256) qsim_jit_delta(u64 n, u64* out) {\n"
+         "  u64 acc = 0;\n"
+         "  const u32 valid = n >= 32ull ? 0xffffffffu : (u32)((1ull << n) - 1ull);\n"
+         "  for (u64 my = ((u64)blockIdx.x * 256ull + threadIdx.x) * 32ull; my < n;"
+         " my += (u64)gridDim.x * 256ull * 32ull) {\n";
+    for (uint32_t b = 0; b < M; ++b) {
+        if (b < 5)
+            s << "    u32 p" << b << " = " << kLanePattern[b] << ";\n";
+        else
+            s << "    u32 p" << b << " = 0u - (u32)((my >> " << b << ") & 1ull);\n";
+    }
+    step_lines(s, steps, n);
+    for (uint32_t b = 0; b < M; ++b) {
+        s << "    acc |= (u64)(((p" << b << " ^ ";
+        if (b < 5) s << kLanePattern[b];
+        else s << "(0u - (u32)((my >> " << b << ") & 1ull))";
+        s << ") & valid) != 0u) << " << b << ";\n";
+    }
+    s << "  }\n"
+         "  u32 lo = (u32)acc, hi = (u32)(acc >> 32);\n"
+         "  lo = __reduce_or_sync(0xffffffffu, lo);\n"
+         "  hi = __reduce_or_sync(0xffffffffu, hi);\n"
+         "  if ((threadIdx.x & 31) == 0 && (lo | hi)) atomicOr(out, ((u64)hi << 32) | lo);\n"
+         "}\n";
+    return s.str();
+}
+
 // CUDA source of one circuit-specialised gather kernel.  Output index
 // my + j (j = 0..31) of a thread is held as 32-bit planes p0..p{M-1};
 // the steps are emitted last to first.
@@ -163,23 +224,7 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
         else
             s << "    u32 p" << b << " = 0u - (u32)((my >> " << b << ") & 1ull);\n";
     }
-    for (size_t q = n; q-- > 0;) {
-        const qsim_step &st = steps[q];
-        s << "    p" << st.target;
-        if (st.ctrl_mask == 0) {
-            s << " = ~p" << st.target << ";\n";
-            continue;
-        }
-        s << " ^= ";
-        bool first = true;
-        for (uint64_t m = st.ctrl_mask; m; m &= m - 1) {
-            const uint32_t b = (uint32_t)__builtin_ctzll(m);
-            if (!first) s << " & ";
-            first = false;
-            s << (((st.ctrl_pol >> b) & 1ull) ? "p" : "~p") << b;
-        }
-        s << ";\n";
-    }
+    step_lines(s, steps, n);
     s << "    u32 r[32];\n";
     for (uint32_t b = 0; b < 32; ++b) {
         if (b < M)
@@ -222,11 +267,251 @@ std::string generate_source(uint32_t M, int amp, const qsim_step *steps, size_t 
     return s.str();
 }
 
-// Compile (or find) the kernel; with load = true also load it on the device.
-int jit_get(uint32_t M, int amp, const qsim_step *steps, size_t n, bool load, JitEntry **out,
-            std::string *msg)
+// Closed tile pass of one circuit: every output row's source lies in its own
+// tile (the circuit's net map changes only tile bits), so a tile is loaded
+// into shared memory by tensor-map copies, each output's source is found by
+// evaluating the circuit on bit planes, and the tile is written back in place.
+const char *kClosedTemplate = R"QSIMSRC(
+typedef unsigned int u32;
+typedef unsigned long long u64;
+typedef unsigned short u16;
+struct __align__(64) TMap { u64 v[16]; };
+struct Params { char *state; double *probs; int *err; u64 n_tiles; u32 wait_limit; u32 pad; };
+#define QSIM_Q __device__ __forceinline__
+#define QSIM_QN __device__ __noinline__
+@PROBMATH@
+@AMPDEF@
+__device__ __forceinline__ u32 sa(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64 *b, u32 c)
+{ asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sa(b)), "r"(c) : "memory"); }
+__device__ __forceinline__ void mbar_expect(u64 *b, u32 bytes)
+{ asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" :: "r"(sa(b)), "r"(bytes) : "memory"); }
+__device__ __forceinline__ void mbar_arrive(u64 *b)
+{ asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(sa(b)) : "memory"); }
+__device__ __forceinline__ bool mbar_wait(u64 *b, u32 parity, u32 limit)
 {
-    std::vector<uint64_t> key = make_key(M, amp, steps, n);
+  for (u32 w = 0; w < limit; ++w) {
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(sa(b)), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma5(void *dst, const TMap *m, int c0, int c1, int c2, int c3, int c4, u64 *bar)
+{
+  asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+               :: "r"(sa(dst)), "l"((u64)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(sa(bar)) : "memory");
+}
+__device__ __forceinline__ void tr32(u32 (&a)[32])
+{
+  u32 m = 0x0000ffffu;
+#pragma unroll
+  for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & j) continue;
+      const u32 t = ((a[k] >> j) ^ a[k | j]) & m;
+      a[k | j] ^= t;
+      a[k] ^= t << j;
+    }
+  }
+}
+#define K @K@
+#define L @L@
+#define NH @NH@
+#define NREST @NREST@
+#define NT @NT@
+#define AB @B@
+#define BOX_BYTES @BOX@
+#define TABN ((NT * 33 + 7) / 8 * 8)  /* exchange-table entries, rounded to 16 bytes */
+__device__ __forceinline__ u64 tile_base(u64 t) { u64 b = 0; @TILEBASE@ return b; }
+__device__ __forceinline__ u64 deposit_high(u32 r) { u64 d = 0; @DEPHIGH@ return d; }
+__device__ __forceinline__ u64 deposit_rest(u32 r) { u64 d = 0; @DEPREST@ return d; }
+extern "C" __global__ void __launch_bounds__(NT + 32, 1)
+qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap tmap)
+{
+  extern __shared__ __align__(128) unsigned char smem[];
+  Amp *buf = reinterpret_cast<Amp *>(smem);
+  u64 *depo = reinterpret_cast<u64 *>(smem + ((size_t)AB << K));
+  u16 *tabs = reinterpret_cast<u16 *>(depo + (1u << NH));
+  u64 *full = reinterpret_cast<u64 *>(tabs + TABN);
+  u64 *empty = full + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (u32 r = tid; r < (1u << NH); r += NT + 32) depo[r] = deposit_high(r);
+  if (tid == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, NT / 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const u64 per = (p.n_tiles + gridDim.x - 1) / gridDim.x;
+  const u64 begin = (u64)blockIdx.x * per;
+  const u64 end = begin + per < p.n_tiles ? begin + per : p.n_tiles;
+  if (warp == NT / 32) {
+    // producer warp: one tile per phase of the single stage
+    for (u64 t = begin; t < end; ++t) {
+      const u32 it = (u32)(t - begin);
+      if (it >= 1 && !mbar_wait(empty, (it - 1) & 1u, p.wait_limit)) {
+        if (lane == 0) atomicOr(p.err, 2);
+        return;
+      }
+      const u64 base = tile_base(t);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) mbar_expect(full, (u32)((size_t)AB << K));
+      __syncwarp();
+      for (u32 r = lane; r < (1u << NREST); r += 32) {
+        const u64 g = base | deposit_rest(r);
+        @COORDS@
+        tma5(reinterpret_cast<char *>(buf) + (size_t)r * BOX_BYTES, &tmap, c0, c1, c2, c3, c4, full);
+      }
+    }
+    return;
+  }
+  // consumer warps: sources of the next tile's outputs while it loads, then
+  // shared memory to global memory in coalesced runs
+  u16 *tab = tabs + warp * 32 * 33;
+  for (u64 t = begin; t < end; ++t) {
+    const u32 it = (u32)(t - begin);
+    const u64 base = tile_base(t);
+    {
+      const u32 j0 = (u32)tid * 32u;
+@PLANES@
+@STEPS@
+@CHECK@
+      u32 r[32];
+@RLOCAL@
+      tr32(r);
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 32; ++u) tab[lane * 33 + u] = (u16)r[u];
+      __syncwarp();
+    }
+    if (!mbar_wait(full, it & 1u, p.wait_limit)) {
+      if (tid == 0) atomicOr(p.err, 1);
+      return;
+    }
+#pragma unroll 1
+    for (int e0 = 0; e0 < 32; e0 += 8) {
+      Amp v[8];
+      u64 g[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const u32 j = ((u32)warp * 32u + (u32)(e0 + u)) * 32u + (u32)lane;
+        v[u] = buf[tab[(e0 + u) * 33 + lane]];
+        g[u] = base + depo[j >> L] + (j & ((1u << L) - 1u));
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        reinterpret_cast<Amp *>(p.state)[g[u]] = v[u];
+        if (p.probs) p.probs[g[u]] = AMP_PROB(v[u]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty);
+  }
+}
+)QSIMSRC";
+
+void replace_all(std::string &s, const std::string &from, const std::string &to)
+{
+    for (size_t pos = 0; (pos = s.find(from, pos)) != std::string::npos; pos += to.size())
+        s.replace(pos, from.size(), to);
+}
+
+// Local bit q of a tile -> address bit (low run first, then the high bits in
+// the layout's order: the order of the amplitudes in shared memory).
+std::vector<uint32_t> tile_local_bits(const TilePass &t)
+{
+    std::vector<uint32_t> lb;
+    for (uint32_t q = 0; q < t.l; ++q) lb.push_back(q);
+    for (uint32_t q = 0; q < t.nh; ++q) lb.push_back(t.high[q]);
+    return lb;
+}
+
+std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
+{
+    std::string src = kClosedTemplate;
+    const std::vector<uint32_t> lb = tile_local_bits(t);
+    const uint32_t K = t.k;
+    std::vector<int> local_of(64, -1);
+    for (uint32_t q = 0; q < K; ++q) local_of[lb[q]] = (int)q;
+    std::ostringstream planes, check, rl, tb, dh, dr, co;
+    for (uint32_t b = 0; b < M; ++b) {
+        const int q = local_of[b];
+        planes << "      u32 p" << b << " = ";
+        if (q >= 0 && q < 5) planes << kLanePattern[q] << ";\n";
+        else if (q >= 5) planes << "0u - ((j0 >> " << q << ") & 1u);\n";
+        else planes << "0u - (u32)((base >> " << b << ") & 1ull);\n";
+    }
+    check << "      u32 viol = 0u;\n";
+    for (uint32_t b = 0; b < M; ++b)
+        if (local_of[b] < 0) check << "      viol |= p" << b << " ^ (0u - (u32)((base >> " << b << ") & 1ull));\n";
+    check << "      if (viol) atomicOr(p.err, 4);\n";
+    for (uint32_t q = 0; q < 32; ++q) {
+        rl << "      r[" << q << "] = ";
+        if (q < K) rl << "p" << lb[q] << ";\n";
+        else rl << "0u;\n";
+    }
+    for (uint32_t q = 0; q < t.nout; ++q) tb << "if ((t >> " << q << ") & 1ull) b |= 1ull << " << t.outpos[q] << "; ";
+    for (uint32_t q = 0; q < t.nh; ++q) dh << "if ((r >> " << q << ") & 1u) d |= 1ull << " << t.high[q] << "; ";
+    for (uint32_t q = 0; q < t.nrest; ++q) dr << "if ((r >> " << q << ") & 1u) d |= 1ull << " << t.rest_pos[q] << "; ";
+    const uint32_t epa = amp == 16 ? 2 : 1;
+    for (int d = 0; d < 5; ++d) {
+        const uint32_t w = t.tma_start[d + 1] - t.tma_start[d];
+        co << "        const int c" << d << " = ";
+        if (w == 0) co << "0;\n";
+        else co << "(int)(((g >> " << t.tma_start[d] << ") & " << ((1ull << w) - 1ull) << "ull)"
+                << (d == 0 && epa == 2 ? " * 2ull" : "") << ");\n";
+    }
+    std::ostringstream st;
+    step_lines(st, steps, n);
+    replace_all(src, "@PROBMATH@", kProbMathSource);
+    replace_all(src, "@AMPDEF@", amp == 16
+                ? "struct __align__(16) Amp { u32 a, b, c, d; };\n#define AMP_PROB(v) qsim_prob_bits((v).a, (v).b, (v).c, (v).d)"
+                : "struct __align__(8) Amp { u32 a, b; };\n#define AMP_PROB(v) qsim_prob_bits((v).a, (v).b)");
+    replace_all(src, "@K@", std::to_string(K));
+    replace_all(src, "@L@", std::to_string(t.l));
+    replace_all(src, "@NH@", std::to_string(t.nh));
+    replace_all(src, "@NREST@", std::to_string(t.nrest));
+    replace_all(src, "@NT@", std::to_string((1u << K) / 32));
+    replace_all(src, "@B@", std::to_string(amp));
+    replace_all(src, "@BOX@", std::to_string(t.box_bytes));
+    replace_all(src, "@TILEBASE@", tb.str());
+    replace_all(src, "@DEPHIGH@", dh.str());
+    replace_all(src, "@DEPREST@", dr.str());
+    replace_all(src, "@COORDS@", co.str());
+    replace_all(src, "@PLANES@", planes.str());
+    replace_all(src, "@STEPS@", st.str());
+    replace_all(src, "@CHECK@", check.str());
+    replace_all(src, "@RLOCAL@", rl.str());
+    return src;
+}
+
+std::vector<uint64_t> closed_key(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
+{
+    std::vector<uint64_t> k = {0xC105EDull, M, (uint64_t)amp, t.k, t.l, t.nh, t.nrest, t.box_bytes, t.nout};
+    for (uint32_t q = 0; q < t.nh; ++q) k.push_back(t.high[q]);
+    for (uint32_t q = 0; q < t.nrest; ++q) k.push_back(t.rest_pos[q]);
+    for (uint32_t q = 0; q < 6; ++q) k.push_back(t.tma_start[q]);
+    for (uint32_t q = 0; q < t.nout; ++q) k.push_back(t.outpos[q]);
+    const std::vector<uint64_t> sk = make_key(M, amp, steps, n);
+    k.insert(k.end(), sk.begin() + 2, sk.end());
+    return k;
+}
+
+// Changed-bit sets already found, keyed by (M, steps).
+std::mutex g_delta_mu;
+std::unordered_map<uint64_t, std::pair<std::vector<uint64_t>, uint64_t>> g_delta_cache;
+
+// Compile (or find) a generated kernel; with load = true also load it on the
+// device.  key identifies the source completely (kind, sizes, layout, steps);
+// gen writes the source on a miss.
+template <typename Gen>
+int jit_get_kernel(std::vector<uint64_t> key, const char *kernel_name, Gen gen, bool load,
+                   JitEntry **out, std::string *msg)
+{
     const uint64_t h = fnv1a(key);
     std::lock_guard<std::mutex> lk(g_jit_mu);
     auto it = g_jit_cache.find(h);
@@ -240,7 +525,7 @@ int jit_get(uint32_t M, int amp, const qsim_step *steps, size_t n, bool load, Ji
             return QSIM_ECUDA;
         }
         const auto t0 = std::chrono::steady_clock::now();
-        const std::string src = generate_source(M, amp, steps, n);
+        const std::string src = gen();
         nvrtcProgram prog;
         nvrtcResult r = nv.create(&prog, src.c_str(), "qsim_jit.cu", 0, nullptr, nullptr);
         if (r != NVRTC_SUCCESS) {
@@ -273,15 +558,23 @@ int jit_get(uint32_t M, int amp, const qsim_step *steps, size_t n, bool load, Ji
     if (load && !e->kern) {
         cudaError_t ce = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr,
                                              nullptr, 0);
-        if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e->kern, e->lib, "qsim_jit_gather");
+        if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e->kern, e->lib, kernel_name);
         if (ce != cudaSuccess) {
             e->kern = nullptr;
-            *msg = std::string("loading the compiled gather: ") + cudaGetErrorString(ce);
+            *msg = std::string("loading a compiled kernel: ") + cudaGetErrorString(ce);
             return QSIM_ECUDA;
         }
     }
     *out = e;
     return QSIM_OK;
+}
+
+// The compiled gather of one segment.
+int jit_get(uint32_t M, int amp, const qsim_step *steps, size_t n, bool load, JitEntry **out,
+            std::string *msg)
+{
+    return jit_get_kernel(make_key(M, amp, steps, n), "qsim_jit_gather",
+                          [&] { return generate_source(M, amp, steps, n); }, load, out, msg);
 }
 
 }  // namespace
@@ -320,6 +613,118 @@ int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim
                                       args, 0, static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) {
         *msg = std::string("compiled gather launch: ") + cudaGetErrorString(ce);
+        return QSIM_ECUDA;
+    }
+    return QSIM_OK;
+}
+
+int jit_delta(uint32_t M, const qsim_step *steps, size_t n, uint64_t *d_word, void *stream,
+              uint64_t *delta, std::string *msg)
+{
+    std::vector<uint64_t> key = make_key(M, 0, steps, n);
+    key[1] = 0xDE17Aull;  // a kernel kind of its own
+    const uint64_t h = fnv1a(key);
+    {
+        std::lock_guard<std::mutex> lk(g_delta_mu);
+        auto it = g_delta_cache.find(h);
+        if (it != g_delta_cache.end() && it->second.first == key) {
+            *delta = it->second.second;
+            return QSIM_OK;
+        }
+    }
+    JitEntry *e = nullptr;
+    int rc = jit_get_kernel(key, "qsim_jit_delta", [&] { return generate_delta_source(M, steps, n); },
+                            true, &e, msg);
+    if (rc != QSIM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaMemsetAsync(d_word, 0, sizeof(uint64_t), s);
+    const uint64_t total = 1ull << M;
+    const uint64_t groups = (total + 256ull * 32 - 1) / (256ull * 32);
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    const unsigned grid = (unsigned)(groups < cap ? groups : cap);
+    uint64_t a0 = total;
+    uint64_t *a1 = d_word;
+    void *args[] = {(void *)&a0, (void *)&a1};
+    if (ce == cudaSuccess)
+        ce = cudaLaunchKernel(reinterpret_cast<const void *>(e->kern), dim3(grid), dim3(256), args, 0, s);
+    uint64_t out = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&out, d_word, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        *msg = std::string("changed-bit kernel: ") + cudaGetErrorString(ce);
+        return QSIM_ECUDA;
+    }
+    *delta = out;
+    std::lock_guard<std::mutex> lk(g_delta_mu);
+    g_delta_cache[h] = {std::move(key), out};
+    return QSIM_OK;
+}
+
+namespace {
+
+struct ClosedParams {
+    char *state;
+    double *probs;
+    int *err;
+    uint64_t n_tiles;
+    uint32_t wait_limit;
+    uint32_t pad;
+};
+
+size_t closed_smem_bytes(int amp, const TilePass &t)
+{
+    const size_t nt = ((size_t)1 << t.k) / 32;
+    const size_t tabn = (nt * 33 + 7) / 8 * 8;
+    return ((size_t)amp << t.k) + sizeof(uint64_t) * ((size_t)1 << t.nh) + 2 * tabn + 2 * sizeof(uint64_t);
+}
+
+int closed_get(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t, JitEntry **e,
+               std::string *msg)
+{
+    // at least one consumer warp (32 threads x 32 outputs) besides the producer
+    if (t.k < 10 || t.k > (uint32_t)kMaxTileBits || t.nh > (uint32_t)kMaxHighBitsClosed ||
+        t.nrest > t.nh || t.l < 1) {
+        *msg = "closed tile pass: tile width outside [10, 14]";
+        return QSIM_EINVAL;
+    }
+    return jit_get_kernel(closed_key(M, amp, steps, n, t), "qsim_jit_closed",
+                          [&] { return generate_closed_source(M, amp, steps, n, t); }, true, e, msg);
+}
+
+}  // namespace
+
+int jit_prepare_closed(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t,
+                       std::string *msg)
+{
+    JitEntry *e = nullptr;
+    return closed_get(M, amp, steps, n, t, &e, msg);
+}
+
+int launch_jit_closed(void *state, int amp, uint32_t M, const qsim_step *steps, size_t n,
+                      const TilePass &t, double *d_probs, int *d_err, void *stream, std::string *msg)
+{
+    JitEntry *e = nullptr;
+    int rc = closed_get(M, amp, steps, n, t, &e, msg);
+    if (rc != QSIM_OK) return rc;
+    alignas(64) unsigned char tmap[128];
+    std::memset(tmap, 0, sizeof(tmap));
+    if (!t.tma || encode_tile_map(state, t, tmap) != 0) {
+        *msg = "closed tile pass: the tile layout has no tensor map";
+        return QSIM_ECUDA;
+    }
+    const size_t smem = closed_smem_bytes(amp, t);
+    cudaError_t ce = cudaFuncSetAttribute(reinterpret_cast<const void *>(e->kern),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ClosedParams p{static_cast<char *>(state), d_probs, d_err, t.n_tiles, 1u << 24, 0u};
+    const uint64_t cap = (uint64_t)num_sms();
+    const unsigned grid = (unsigned)(t.n_tiles < cap ? t.n_tiles : cap);
+    const unsigned block = (unsigned)((1u << t.k) / 32 + 32);
+    void *args[] = {(void *)&p, (void *)tmap};
+    if (ce == cudaSuccess)
+        ce = cudaLaunchKernel(reinterpret_cast<const void *>(e->kern), dim3(grid), dim3(block), args, smem,
+                              static_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) {
+        *msg = std::string("closed tile pass launch: ") + cudaGetErrorString(ce);
         return QSIM_ECUDA;
     }
     return QSIM_OK;

@@ -1124,6 +1124,23 @@ size_t tile_smem_bytes(int amp_bytes, int k)
            sizeof(uint32_t) * kMaxOutBits + sizeof(uint16_t) * ((size_t)1 << k);
 }
 
+int encode_tile_map(void *state, const TilePass &t, void *map128)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return 1;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    for (int d = 0; d < 5; ++d) {
+        dims[d] = t.tma_dim[d];
+        box[d] = t.tma_box[d];
+    }
+    for (int d = 1; d < 5; ++d) strides[d - 1] = t.tma_stride[d];
+    CUresult r = enc(static_cast<CUtensorMap *>(map128), CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, state, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : 2;
+}
+
 int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d_steps,
                 int *d_err, double *d_probs, void *stream, const WaitTest *wt)
 {
@@ -1154,22 +1171,9 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
     if (t.tma) {
-        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-        if (!enc) {
-            p.tma = 0;  // no driver entry point: one bulk copy per run
-        } else {
-            cuuint64_t dims[5], strides[4];
-            cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
-            for (int d = 0; d < 5; ++d) {
-                dims[d] = t.tma_dim[d];
-                box[d] = t.tma_box[d];
-            }
-            for (int d = 1; d < 5; ++d) strides[d - 1] = t.tma_stride[d];
-            CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, state, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        }
+        const int te = encode_tile_map(state, t, &tmap);
+        if (te == 1) p.tma = 0;  // no driver entry point: one bulk copy per run
+        else if (te != 0) return cudaErrorInvalidValue;
     }
     const size_t smem = tile_smem_bytes(amp_bytes, (int)t.k);
     const uint64_t cap = (uint64_t)num_sms();

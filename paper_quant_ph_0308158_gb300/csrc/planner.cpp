@@ -720,6 +720,8 @@ constexpr double kEffRandom = 0.50;
 constexpr double kSlicedStepS = 2.8e-14;  // per step and output, interpreter
 constexpr double kCompiledStepS = 2.2e-15; // per step and output, compiled kernel
 constexpr double kLaunchS = 4e-6;
+constexpr double kEffClosed = 0.75;        // closed pass: tile streaming with 64-byte runs
+constexpr double kClosedStepS = 1.2e-15;   // per step and output, planes in registers
 
 double gather_cost_s(uint32_t M, size_t amp, bool affine, bool coset, bool compiled, size_t nsteps)
 {
@@ -733,6 +735,13 @@ double gather_cost_s(uint32_t M, size_t amp, bool affine, bool coset, bool compi
 double pass_cost_s(const Pass &p, uint32_t M, size_t amp)
 {
     if (p.kind == kSweep) return kLaunchS + p.alg_bytes / (kEffSweep * kPeakBytesPerS);
+    if (p.kind == kTile && p.tile.closed) {
+        // streaming and per-output evaluation overlap (the next tile's
+        // sources are found while it loads)
+        const double mem = p.alg_bytes / (kEffClosed * kPeakBytesPerS);
+        const double alu = (double)p.tile.jit_n * (double)(1ull << M) * kClosedStepS;
+        return kLaunchS + std::max(mem, alu) + 0.25 * std::min(mem, alu);
+    }
     if (p.kind == kTile) return kLaunchS + p.alg_bytes / (kEffTile * kPeakBytesPerS);
     const GatherPass &g = p.gather;
     return gather_cost_s(M, amp, g.affine != 0, g.coset != 0, g.jit != 0,
@@ -845,6 +854,51 @@ bool plan_hybrid(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
     return true;
 }
 
+// Closed tile pass: when the circuit's net row map changes only the address
+// bits in delta (the OR over all rows of x(i) ^ i, found on the device), every
+// output's source lies in the same coset of those bits.  A tile over delta,
+// filled up from bit 0 to the widest tile shared memory holds (so that the
+// low address bits give contiguous runs), then holds every source of its
+// outputs, and one in-place pass applies the whole circuit: Sec. 2i's
+// grouping of sequential steps taken to a whole circuit, with the Sec. 2h
+// product evaluated per output.  Needs compiled kernels.
+bool plan_closed(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &order,
+                 const PlanOptions &o, Plan *plan)
+{
+    if (!o.jit || !o.closed_known || order.empty()) return false;
+    const uint32_t kmax = std::min<uint32_t>(o.amp_bytes == 16 ? 13 : 14, M);
+    uint64_t T = o.closed_delta & full_mask(M);
+    if ((uint32_t)popcount64(T) > kmax) return false;
+    for (uint32_t b = 0; b < M && (uint32_t)popcount64(T) < kmax; ++b) T |= 1ull << b;
+    uint32_t l = 0;
+    while (l < M && ((T >> l) & 1ull)) ++l;
+    const uint32_t k = (uint32_t)popcount64(T);
+    if (l < 1 || k < 10 || k - l > (uint32_t)kMaxHighBitsClosed) return false;
+    Pass p{};
+    p.kind = kTile;
+    TilePass &t = p.tile;
+    layout_tile(M, l, T & ~((1ull << l) - 1ull), o.amp_bytes, &t);
+    if (!t.tma || t.k != k) return false;
+    t.closed = 1;
+    t.n_tiles = 1ull << (M - k);
+    t.nout = 0;
+    for (uint32_t b = 0; b < M; ++b)
+        if (!((T >> b) & 1ull)) t.outpos[t.nout++] = b;
+    t.step_off = (uint32_t)plan->tile_steps.size();
+    t.nsteps = 0;
+    t.all_local = 1;
+    t.touched = 1.0;
+    t.jit_off = (uint32_t)plan->jit_steps.size();
+    t.jit_n = (uint32_t)order.size();
+    for (uint64_t idx : order) plan->jit_steps.push_back(steps[idx]);
+    p.nsteps = t.jit_n;
+    p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+    plan->passes.push_back(p);
+    for (uint64_t idx : order) plan->order.push_back(idx);
+    plan->pass_ends.push_back(plan->order.size());
+    return true;
+}
+
 }  // namespace
 
 int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o, Plan *plan,
@@ -894,7 +948,19 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
     tp.steps_in = plan->steps_in;
     tp.cancelled = plan->cancelled;
     plan_tiles(M, steps, order, oo, true, &tp);
-    const double tcost = plan_cost_s(tp, M, oo.amp_bytes);
+    double tcost = plan_cost_s(tp, M, oo.amp_bytes);
+    {
+        Plan cp;
+        cp.steps_in = plan->steps_in;
+        cp.cancelled = plan->cancelled;
+        if (plan_closed(M, steps, order, oo, &cp)) {
+            const double ccost = plan_cost_s(cp, M, oo.amp_bytes);
+            if (ccost < tcost) {
+                tp = std::move(cp);
+                tcost = ccost;
+            }
+        }
+    }
     if (oo.scratch_available) {
         Plan gp;
         gp.steps_in = plan->steps_in;
@@ -944,6 +1010,7 @@ int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<Sl
 
 uint32_t pass_variant(const Pass &p)
 {
+    if (p.kind == kTile && p.tile.closed) return 8;
     if (p.kind != kGather) return (uint32_t)p.kind;
     if (p.gather.affine) return p.gather.coset ? 7 : 3;
     return p.gather.jit ? 5 : 4;

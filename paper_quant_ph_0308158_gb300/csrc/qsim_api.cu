@@ -137,6 +137,9 @@ int check_device(qsim_ctx *c)
     QSIM_CUDA(cudaStreamSynchronize(c->stream), "kernel execution");
     if (flag) {
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        if (flag & 4)
+            return fail(QSIM_ECUDA, "closed tile pass: a source row left its tile (error flag " +
+                                        std::to_string(flag) + ")");
         return fail(QSIM_ETIMEOUT, "a bounded device wait gave up (error flag " +
                                        std::to_string(flag) + ")");
     }
@@ -504,7 +507,22 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     std::string msg;
     PlanOptions o = c->opts;
     o.amp_bytes = c->amp;
-    int rc = make_plan(c->M, steps, L, o, &plan, &msg);
+    int rc = validate_steps(c->M, steps, L, &msg);
+    if (rc != QSIM_OK) return fail(rc, msg);
+    // With compiled kernels, the address bits the circuit's net row map can
+    // change (found once per circuit on the device, then cached) let the
+    // planner weigh a closed tile pass.
+    if (o.jit && (o.strategy == QSIM_STRATEGY_AUTO || o.strategy == QSIM_STRATEGY_INPLACE) &&
+        c->M >= kClosedMinQubits && L >= kClosedMinSteps) {
+        uint64_t delta = 0;
+        std::string dmsg;
+        if (jit_delta(c->M, steps, L, reinterpret_cast<uint64_t *>(c->d_partials), c->stream, &delta, &dmsg) ==
+            QSIM_OK) {
+            o.closed_known = true;
+            o.closed_delta = delta;
+        }
+    }
+    rc = make_plan(c->M, steps, L, o, &plan, &msg);
     if (rc != QSIM_OK) return fail(rc, msg);
     fill_stats(plan, c->M, c->amp, &c->stats);
     if (plan.passes.empty()) return d_probs ? probabilities_pass(c, d_probs) : QSIM_OK;
@@ -518,9 +536,14 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     // compile every circuit-specialised kernel before the first launch, so a
     // compile failure leaves the state untouched
     for (const Pass &p : plan.passes) {
-        if (p.kind != kGather || !p.gather.jit) continue;
         std::string jmsg;
-        rc = jit_prepare(c->M, (int)c->amp, plan.jit_steps.data() + p.gather.jit_off, p.gather.jit_n, &jmsg);
+        if (p.kind == kTile && p.tile.closed)
+            rc = jit_prepare_closed(c->M, (int)c->amp, plan.jit_steps.data() + p.tile.jit_off, p.tile.jit_n,
+                                    p.tile, &jmsg);
+        else if (p.kind == kGather && p.gather.jit)
+            rc = jit_prepare(c->M, (int)c->amp, plan.jit_steps.data() + p.gather.jit_off, p.gather.jit_n, &jmsg);
+        else
+            continue;
         if (rc != QSIM_OK) return fail(rc, jmsg);
     }
     // one contiguous table: tile steps | sliced steps | gather tables
@@ -554,13 +577,19 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
         double bytes = p.alg_bytes;
         if (pp) {
             // every tile is read; touched tiles are written; plus the probabilities
-            bytes = (p.kind == kTile ? n * c->amp + 0.5 * p.alg_bytes : p.alg_bytes) + 8.0 * n;
+            bytes = (p.kind == kTile && !p.tile.closed ? n * c->amp + 0.5 * p.alg_bytes : p.alg_bytes) + 8.0 * n;
             fused = true;
         }
         const int slot = prof_begin(c, pass_variant(p), bytes);
         int e = cudaSuccess;
         if (p.kind == kSweep) {
             e = launch_sweep(c->buf[c->cur], (int)c->amp, p.sweep, c->d_err, c->stream);
+        } else if (p.kind == kTile && p.tile.closed) {
+            std::string jmsg;
+            const int jrc = launch_jit_closed(c->buf[c->cur], (int)c->amp, c->M,
+                                              plan.jit_steps.data() + p.tile.jit_off, p.tile.jit_n, p.tile,
+                                              pp, c->d_err, c->stream, &jmsg);
+            if (jrc != QSIM_OK) return fail(jrc, jmsg);
         } else if (p.kind == kTile) {
             e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, pp, c->stream,
                             c->wait_test_armed ? &c->wait_test : nullptr);
@@ -940,6 +969,8 @@ int qsim_plan_circuit_ex(uint32_t M, int dtype, const qsim_step *steps, size_t L
     o.coset = q.coset != 0;
     o.coset_run_bits = q.coset_run_bits;
     o.cancel_adjacent = q.canonicalize != 0;
+    o.closed_known = q.closed_known != 0;
+    o.closed_delta = q.closed_delta;
     Plan plan;
     std::string msg;
     rc = make_plan(M, steps, L, o, &plan, &msg);

@@ -24,9 +24,12 @@ namespace qsim {
 
 constexpr int kMaxTileBits = 14;      // 2^14 amplitudes per tile at most
 constexpr size_t kMaxTileBytes = 128 * 1024;  // and 128 KiB of shared memory
-constexpr int kMaxHighBits = 10;      // tile bits above the contiguous run
+constexpr int kMaxHighBits = 10;      // tile bits above the contiguous run (tile kernel)
+constexpr int kMaxHighBitsClosed = 13;  // the same for closed passes
 constexpr int kMaxTileSteps = 256;    // steps per tile pass (shared-memory list)
 constexpr int kMaxGatherSteps = 4096; // steps per general gather pass
+constexpr uint32_t kClosedMinQubits = 12;  // circuits examined for a closed pass
+constexpr size_t kClosedMinSteps = 16;
 
 // A tile step in the tile's local coordinates.  Local bit q < l is global bit
 // q; local bit l + p is global bit high[p].  cl/pl: control mask/polarity on
@@ -68,7 +71,7 @@ struct SweepParams {
 
 struct TilePass {
     uint32_t k, l, nh;  // tile width, contiguous low bits, high bits
-    uint32_t high[kMaxHighBits];
+    uint32_t high[kMaxHighBitsClosed];
     uint32_t tma;       // 1: tensor-map copies (else one bulk copy per run)
     uint32_t tma_ndims; // dimensions of the view that carry tile bits
     uint32_t tma_start[6];    // first address bit of each dimension's range
@@ -77,7 +80,7 @@ struct TilePass {
     uint32_t tma_box[5];      // box extents
     uint32_t box_bytes;       // bytes moved by one copy
     uint32_t nrest;           // tile bits enumerated by separate copies
-    uint32_t rest_pos[kMaxHighBits];
+    uint32_t rest_pos[kMaxHighBitsClosed];
     uint32_t nout;      // address bits outside the tile (M - k)
     uint32_t outpos[40];  // their positions, in tile-id bit order: bits that
                           // are controls of some step come last (slowest)
@@ -87,6 +90,12 @@ struct TilePass {
     uint32_t all_local; // 1 when no step has a control outside the tile
     uint32_t affine;    // 1 when every step has at most one control (NOT/CNOT)
     double touched;     // estimated fraction of tiles with an active step
+    // Closed pass (qsim_jit_closed): the segment's net row map changes only
+    // address bits inside the tile, so each tile holds every source of its
+    // outputs; the segment's steps (Plan::jit_steps) are compiled in and
+    // evaluated per output, in place.
+    uint32_t closed;
+    uint32_t jit_off, jit_n;
 };
 
 struct GatherPass {
@@ -115,8 +124,8 @@ struct GatherPass {
 
 enum PassKind : uint32_t { kSweep = 1, kTile = 2, kGather = 3 };
 // Kernel variant reported by tracing: 1 sweep, 2 tile, 3 affine gather,
-// 4 bit-sliced gather, 5 compiled gather, 7 coset-blocked affine gather
-// (6 is the probabilities pass).
+// 4 bit-sliced gather, 5 compiled gather, 7 coset-blocked affine gather,
+// 8 closed tile pass (6 is the probabilities pass).
 uint32_t pass_variant(const struct Pass &p);
 
 struct Pass {
@@ -138,6 +147,8 @@ struct PlanOptions {
     bool cancel_adjacent = true;
     bool jit = false;        // compile non-affine gather segments (jit.cu)
     bool coset = true;       // affine segments through coset-blocked tiles
+    bool closed_known = false;  // closed_delta holds the bits the circuit's net map changes
+    uint64_t closed_delta = 0;
     int coset_run_bits = 0;  // r of those tiles (0: runs of 512 bytes)
     int jit_min_steps = 32;  // shorter segments use the general kernel
 };
@@ -223,6 +234,9 @@ int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<Sl
 int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
                        uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream);
 size_t tile_smem_bytes(int amp_bytes, int k);
+// The tensor map (128 bytes) of a tile layout over a state: 0 on success, 1
+// without the driver's encoder, 2 when the driver rejects the layout.
+int encode_tile_map(void *state, const TilePass &t, void *map128);
 // Shared memory of a coset-gather launch and its pipeline depth.
 size_t coset_smem_bytes(int amp_bytes, uint32_t r, uint32_t d, uint32_t e, uint32_t *stages);
 
@@ -233,6 +247,16 @@ int jit_compile(uint32_t M, int amp, const qsim_step *steps, size_t n, double *c
 int jit_prepare(uint32_t M, int amp, const qsim_step *steps, size_t n, std::string *msg);
 int launch_jit_gather(const void *in, void *out, int amp, uint32_t M, const qsim_step *steps,
                       size_t n, double *d_probs, void *stream, std::string *msg);
+// The address bits that the row map of a step list can change: OR over every
+// row i of x(i) ^ i, evaluated on the device (compiled, cached by steps).
+// d_word: 8 bytes of device scratch; synchronises the stream.
+int jit_delta(uint32_t M, const qsim_step *steps, size_t n, uint64_t *d_word, void *stream,
+              uint64_t *delta, std::string *msg);
+// Closed tile pass: compile ahead of its launch (cached), and launch.
+int jit_prepare_closed(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t,
+                       std::string *msg);
+int launch_jit_closed(void *state, int amp, uint32_t M, const qsim_step *steps, size_t n,
+                      const TilePass &t, double *d_probs, int *d_err, void *stream, std::string *msg);
 int num_sms();
 
 }  // namespace qsim

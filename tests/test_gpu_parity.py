@@ -308,12 +308,20 @@ def test_mixed_m28_workload_inplace_sampled():
 
 
 def test_adder_m32_workload_sampled():
-    """M=32 complex64 (32 GiB) adder, in place, as benchmarked: tile passes,
-    the last one also writing the FP64 probabilities (bit-exact for
+    """M=32 complex64 (32 GiB) adder, in place, tile passes (compiled kernels
+    off), the last one also writing the FP64 probabilities (bit-exact for
     complex64, whose squares are exact)."""
     st, kernels = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 18, probs=True)
     assert st["gather_passes"] == 0 and st["passes"] >= 1
     assert set(kernels) <= {"tile_kernel", "sweep_kernel"} and kernels[-1] == "tile_kernel"
+
+
+def test_adder_m32_benchmarked_closed_pass_sampled():
+    """M=32 complex64 adder in place as benchmarked: compiled kernels on, so
+    the whole circuit is one closed tile pass (its net map changes only
+    b_4..b_14 and the carry-out) that also writes the probabilities."""
+    st, kernels = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 20, jit=True, probs=True)
+    assert st["passes"] == 1 and kernels == ["qsim_jit_closed"]
 
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])

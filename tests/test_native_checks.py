@@ -120,3 +120,100 @@ def test_compiled_gather_source_evaluates_the_inverse_circuit(tmp_path, M, L, se
                     x ^= 1 << int(s["target"])
             got = sum(((planes[b] >> j) & 1) << b for b in range(M))
             assert got == x, (M, i)
+
+
+def _closed_dump(tmp_path, M, amp, steps, delta, compile_=False):
+    exe = tmp_path / "closed_source_dump"
+    if not exe.exists():
+        subprocess.run(["g++", "-O1", "-std=c++17", "-I", "/usr/local/cuda/include", "-x", "c++", "-o", str(exe),
+                        os.path.join(ROOT, "tests", "native", "closed_source_dump.cpp"),
+                        "-L/usr/local/cuda/lib64", "-lcudart", "-ldl"], check=True)
+    text = "%d %d %d %d\n" % (M, amp, len(steps), delta) + "".join(
+        "%d %d %d\n" % (int(s["target"]), int(s["ctrl_mask"]), int(s["ctrl_pol"])) for s in steps)
+    env = dict(os.environ, LD_LIBRARY_PATH="/usr/local/cuda/lib64:" + os.environ.get("LD_LIBRARY_PATH", ""))
+    r = subprocess.run([str(exe)] + (["--compile"] if compile_ else []), input=text, capture_output=True,
+                       text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr
+    return r.stdout
+
+
+def _eval_closed(src: str, M: int, base: int, tid: int):
+    """Evaluate the generated closed kernel's plane set-up, steps and local
+    source read-out for thread tid of the tile at 'base'; returns the 32
+    local source indices."""
+    import re
+    mask = 0xFFFFFFFF
+    planes, r = {}, {}
+    j0 = tid * 32
+    for line in src.splitlines():
+        line = line.strip()
+        m = re.fullmatch(r"u32 p(\d+) = (0x[0-9a-f]+)u;", line)
+        if m:
+            planes[int(m.group(1))] = int(m.group(2), 16)
+            continue
+        m = re.fullmatch(r"u32 p(\d+) = 0u - \(\(j0 >> (\d+)\) & 1u\);", line)
+        if m:
+            planes[int(m.group(1))] = mask if (j0 >> int(m.group(2))) & 1 else 0
+            continue
+        m = re.fullmatch(r"u32 p(\d+) = 0u - \(u32\)\(\(base >> (\d+)\) & 1ull\);", line)
+        if m:
+            planes[int(m.group(1))] = mask if (base >> int(m.group(2))) & 1 else 0
+            continue
+        m = re.fullmatch(r"p(\d+) = ~p(\d+);", line)
+        if m:
+            planes[int(m.group(1))] = ~planes[int(m.group(2))] & mask
+            continue
+        m = re.fullmatch(r"p(\d+) \^= (.+);", line)
+        if m:
+            acc = mask
+            for term in m.group(2).split(" & "):
+                v = planes[int(term.lstrip("~p"))]
+                acc &= (~v & mask) if term.startswith("~") else v
+            planes[int(m.group(1))] ^= acc
+            continue
+        m = re.fullmatch(r"r\[(\d+)\] = (p(\d+)|0u);", line)
+        if m:
+            r[int(m.group(1))] = planes[int(m.group(3))] if m.group(3) else 0
+    return [sum(((r[q] >> u) & 1) << q for q in range(32)) for u in range(32)]
+
+
+@pytest.mark.parametrize("amp", [8, 16])
+def test_closed_pass_source_finds_every_source_in_its_tile(tmp_path, amp):
+    """The generated closed tile pass for the M=32 ripple-carry adder (its
+    net map changes only b_4..b_14 and the carry-out: 16 additions of a leave
+    b's low four bits alone), evaluated on the host for sampled tiles and
+    threads: each output's source, read from the tile's local order, is the
+    oracle's x(i).  The source also compiles with NVRTC for sm_103a."""
+    import numpy as np
+    import oracle
+    from paper_quant_ph_0308158_gb300 import workloads as W
+    cfg = W.config_adder_m32()
+    l2b = cfg["line_to_bit"]
+    cin, a, b, cout = W.adder_lines(15)
+    delta = 0
+    for x in b[4:] + [cout]:
+        delta |= 1 << l2b[x]
+    out = _closed_dump(tmp_path, 32, amp, cfg["steps"], delta, compile_=(amp == 8))
+    lay = [l for l in out.splitlines() if l.startswith("@LAYOUT")][0].split()[1:]
+    outs = [int(x) for x in [l for l in out.splitlines() if l.startswith("@OUT")][0].split()[1:]]
+    l, k = int(lay[0]), int(lay[1])
+    lb = list(range(l)) + [int(x) for x in lay[2:]]
+    assert len(lb) == k and (delta & ~sum(1 << x for x in lb)) == 0
+    if amp == 8:
+        assert "compiled" in out.splitlines()[-1]
+
+    def deposit(v, bits):
+        return sum(((v >> q) & 1) << bit for q, bit in enumerate(bits))
+
+    rng = np.random.default_rng(amp)
+    rows, srcs = [], []
+    for _ in range(6):
+        t = int(rng.integers(0, 1 << len(outs)))
+        base = deposit(t, outs)
+        for tid in rng.integers(0, (1 << k) // 32, size=3):
+            loc = _eval_closed(out, 32, base, int(tid))
+            for u in range(32):
+                rows.append(base | deposit(int(tid) * 32 + u, lb))
+                srcs.append(base | deposit(loc[u], lb))
+    want = oracle.source_rows(32, cfg["steps"], np.array(rows, dtype=np.uint64))
+    np.testing.assert_array_equal(np.array(srcs, dtype=np.uint64), want)
