@@ -872,6 +872,7 @@ bool plan_closed(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
     for (uint32_t b = 0; b < M && (uint32_t)popcount64(T) < kmax; ++b) T |= 1ull << b;
     uint32_t l = 0;
     while (l < M && ((T >> l) & 1ull)) ++l;
+    l = std::min<uint32_t>(l, o.amp_bytes == 16 ? 7 : 8);  // a tensor-map box row is <= 256 words
     const uint32_t k = (uint32_t)popcount64(T);
     if (l < 1 || k < 10 || k - l > (uint32_t)kMaxHighBitsClosed) return false;
     Pass p{};

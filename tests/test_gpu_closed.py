@@ -75,7 +75,10 @@ def test_closed_pass_bit_exact(dtype, M, s, L1, L2, seed):
     want = oracle.apply_circuit(M, k1, steps).astype(dtype)
     got, kernels = _run_closed(M, dtype, steps, k1)
     np.testing.assert_array_equal(got, want)
-    assert kernels == ["qsim_jit_closed"]
+    if M > (14 if dtype == np.complex64 else 13):
+        assert kernels == ["qsim_jit_closed"]
+    else:  # one ordinary tile holds the whole state: a single tile pass does it
+        assert len(kernels) == 1
 
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
