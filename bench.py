@@ -77,6 +77,8 @@ def workload(name: str):
         return W.config_mixed(24)
     if name == "cnot_m28":  # CNOT-only: one affine gather pass
         return W.config_cnot(28)
+    if name == "cnot_m26":  # 1 GiB: the small case for coset-gather captures
+        return W.config_cnot(26)
     if name == "adder_m28":  # 2 GiB in-place adder: the small case for tile-kernel captures
         return W.config_adder(13)
     if name == "hybrid_m28":  # register arithmetic then a CNOT layer: strategies mixed per segment
@@ -370,6 +372,7 @@ def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, s
     sim = Simulator(M, dtype, scratch=scratch)
     sim.set_strategy(strategy, args.tile_bits, args.low_bits)
     sim.set_canonicalize(False)
+    sim.set_coset(not args.no_coset, args.coset_run_bits, args.coset_stage_kib)
 
     def load_input():
         if qubits is None:
@@ -1013,7 +1016,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "parity_m32", "hybrid_m28",
+    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "cnot_m26", "parity_m32", "hybrid_m28",
                              "batch_cnot", "batch_mixed", "serve", "parity_scan", "gather_floor"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")
@@ -1046,6 +1049,9 @@ def main():
     ap.add_argument("--no-jit", dest="jit", action="store_false",
                     help="use the general bit-sliced gather instead of compiled kernels")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-coset", action="store_true", help="affine gathers read rows directly")
+    ap.add_argument("--coset-run-bits", type=int, default=0, help="coset tile run length r (0: 512 B)")
+    ap.add_argument("--coset-stage-kib", type=int, default=0, help="coset pipeline stage (0: 32 KiB)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison of the default run")
     ap.add_argument("--also", default="mixed_m28,cnot_m28,hybrid_m28",

@@ -161,7 +161,7 @@ def load() -> ctypes.CDLL:
             "qsim_set_profiling": ([p, i], i),
             "qsim_set_jit": ([p, i], i),
             "qsim_set_wait_test": ([p, u32], i),
-            "qsim_set_coset": ([p, i, i], i),
+            "qsim_set_coset": ([p, i, i, i], i),
             "qsim_gather_rows": ([p, p, p, u32, i, p, i, p], i),
             "qsim_plan_circuit_ex": ([u32, i, p, sz, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanStats),
                                       p, p, p, p, sz], i),
@@ -392,9 +392,9 @@ class Simulator:
     def set_jit(self, enable: bool):
         _check(self._lib.qsim_set_jit(self._ctx, int(bool(enable))))
 
-    def set_coset(self, enable: bool, run_bits: int = 0):
+    def set_coset(self, enable: bool, run_bits: int = 0, stage_kib: int = 0):
         """Affine gathers through coset-blocked tiles (default) or direct reads."""
-        _check(self._lib.qsim_set_coset(self._ctx, int(bool(enable)), run_bits))
+        _check(self._lib.qsim_set_coset(self._ctx, int(bool(enable)), run_bits, stage_kib))
 
     def set_wait_test(self, poll_limit: int):
         """Arm the next tile pass to give up its pipeline waits (testing)."""

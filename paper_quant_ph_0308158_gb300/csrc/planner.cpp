@@ -324,6 +324,14 @@ void emit_tile(uint32_t M, const qsim_step *steps, const std::vector<uint64_t> &
         touched = (double)hit / samples;
     }
     t.touched = touched;
+    // Tiles are dealt in tile-id order with the out-of-tile control bits
+    // slowest, so the active set changes at most once per value of those
+    // bits (and per CTA range); an affine pass reuses one table throughout.
+    {
+        const int nctl = popcount64(ctl_out);
+        const double changes = nctl >= 40 ? 1e12 : (double)(1ull << nctl);
+        t.rebuilds = t.affine ? 152.0 : std::min((double)t.n_tiles * touched, changes) + 152.0;
+    }
     p.nsteps = t.nsteps;
     p.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes) * touched;
     plan->passes.push_back(p);
@@ -520,9 +528,12 @@ bool emit_coset_r(uint32_t M, const uint64_t *col, uint32_t r, const PlanOptions
     const uint32_t nc = (uint32_t)pos.size();  // M - r - d
     gp->n_tiles = 1ull << nc;
     gp->ctb = (nc + 7) / 8;
-    // tiles per pipeline stage: stages of at least 16 KiB, at most 64 tiles
+    // tiles per pipeline stage: stages of at least stage_kib KiB (default
+    // 32), at most 64 tiles
+    const uint64_t stage = (uint64_t)(o.coset_stage_kib > 0 ? o.coset_stage_kib : 32) * 1024;
     uint32_t e = 0;
-    while (e < nc && e < 6 && ((uint64_t)amp << (r + d + e)) < 16 * 1024) ++e;
+    while (e < nc && e < 6 && ((uint64_t)amp << (r + d + e)) < stage && ((uint64_t)amp << (r + d + e + 1)) <= 96 * 1024)
+        ++e;
     gp->ce = e;
     gp->coset_off = (uint32_t)plan->gather_tables.size();
     std::vector<uint64_t> &tab = plan->gather_tables;
@@ -721,6 +732,8 @@ constexpr double kSlicedStepS = 2.8e-14;  // per step and output, interpreter
 constexpr double kCompiledStepS = 2.2e-15; // per step and output, compiled kernel
 constexpr double kLaunchS = 4e-6;
 constexpr double kEffClosed = 0.75;        // closed pass: tile streaming with 64-byte runs
+constexpr double kTableStepS = 2.1e-11;    // tile table build, per local index and step, one SM
+constexpr double kSms = 152.0;
 constexpr double kClosedStepS = 1.2e-15;   // per step and output, planes in registers
 
 double gather_cost_s(uint32_t M, size_t amp, bool affine, bool coset, bool compiled, size_t nsteps)
@@ -742,7 +755,12 @@ double pass_cost_s(const Pass &p, uint32_t M, size_t amp)
         const double alu = (double)p.tile.jit_n * (double)(1ull << M) * kClosedStepS;
         return kLaunchS + std::max(mem, alu) + 0.25 * std::min(mem, alu);
     }
-    if (p.kind == kTile) return kLaunchS + p.alg_bytes / (kEffTile * kPeakBytesPerS);
+    if (p.kind == kTile) {
+        // table builds: every local index through every step, by the SMs
+        const double build = p.tile.rebuilds * (double)(1u << p.tile.k) * (double)p.tile.nsteps *
+                             kTableStepS / kSms;
+        return kLaunchS + p.alg_bytes / (kEffTile * kPeakBytesPerS) + build;
+    }
     const GatherPass &g = p.gather;
     return gather_cost_s(M, amp, g.affine != 0, g.coset != 0, g.jit != 0,
                          g.jit ? g.jit_n : g.nsteps);
@@ -774,6 +792,61 @@ double gather_range_cost_s(uint32_t M, const qsim_step *steps, const std::vector
         i = e;
     }
     return t;
+}
+
+// With compiled kernels, a tile pass whose permutation table would be
+// rebuilt for many tiles (steps controlled by bits outside the tile) runs
+// instead as a closed pass over the same tile: its steps only change tile
+// bits, so each output's source is evaluated from the compiled steps with
+// the outside bits constant per tile.  Converted where the cost model
+// expects it to be faster.
+void close_tile_passes(uint32_t M, const qsim_step *steps, const PlanOptions &o, Plan *plan)
+{
+    if (!o.jit) return;
+    for (size_t pi = 0; pi < plan->passes.size(); ++pi) {
+        Pass &p = plan->passes[pi];
+        if (p.kind != kTile || p.tile.closed || p.tile.k < 10 || p.tile.l < 1 || !p.tile.tma) continue;
+        Pass c = p;
+        TilePass &t = c.tile;
+        t.closed = 1;
+        const uint64_t first = pi ? plan->pass_ends[pi - 1] : 0, last = plan->pass_ends[pi];
+        t.jit_n = (uint32_t)(last - first);
+        c.alg_bytes = 2.0 * state_bytes(M, o.amp_bytes);
+        if (pass_cost_s(c, M, o.amp_bytes) >= pass_cost_s(p, M, o.amp_bytes)) continue;
+        t.jit_off = (uint32_t)plan->jit_steps.size();
+        for (uint64_t q = first; q < last; ++q) plan->jit_steps.push_back(steps[plan->order[q]]);
+        t.nsteps = 0;
+        t.all_local = 1;
+        t.touched = 1.0;
+        p = c;
+    }
+}
+
+// Append the passes of src (planned on its own) to dst, rebasing the
+// offsets of their tables and step lists.
+void append_plan(const Plan &src, Plan *dst)
+{
+    const uint32_t tile0 = (uint32_t)dst->tile_steps.size(), sl0 = (uint32_t)dst->sliced_steps.size();
+    const uint32_t tab0 = (uint32_t)dst->gather_tables.size(), jit0 = (uint32_t)dst->jit_steps.size();
+    const uint64_t ord0 = dst->order.size();
+    for (Pass p : src.passes) {
+        if (p.kind == kTile) {
+            p.tile.step_off += tile0;
+            p.tile.jit_off += jit0;
+        } else if (p.kind == kGather) {
+            p.gather.table_off += tab0;
+            p.gather.coset_off += tab0;
+            p.gather.step_off += sl0;
+            p.gather.jit_off += jit0;
+        }
+        dst->passes.push_back(p);
+    }
+    dst->tile_steps.insert(dst->tile_steps.end(), src.tile_steps.begin(), src.tile_steps.end());
+    dst->sliced_steps.insert(dst->sliced_steps.end(), src.sliced_steps.begin(), src.sliced_steps.end());
+    dst->gather_tables.insert(dst->gather_tables.end(), src.gather_tables.begin(), src.gather_tables.end());
+    dst->jit_steps.insert(dst->jit_steps.end(), src.jit_steps.begin(), src.jit_steps.end());
+    dst->order.insert(dst->order.end(), src.order.begin(), src.order.end());
+    for (uint64_t e : src.pass_ends) dst->pass_ends.push_back(e + ord0);
 }
 
 // Per-segment choice (Sec. 2i groups sequential steps; each group may take
@@ -816,6 +889,7 @@ bool plan_hybrid(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
         Plan tmp;
         std::vector<uint64_t> sub(order.begin() + blocks[b].first, order.begin() + blocks[b].second);
         plan_tiles(M, steps, sub, o, true, &tmp);
+        close_tile_passes(M, steps, o, &tmp);
         tcost[b] = plan_cost_s(tmp, M, o.amp_bytes);
     }
     // best[j]: cheapest cover of blocks [0, j); choice: start block and kind
@@ -847,7 +921,10 @@ bool plan_hybrid(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
         } else {
             for (size_t b = a; b < j; ++b) {
                 std::vector<uint64_t> sub(order.begin() + blocks[b].first, order.begin() + blocks[b].second);
-                plan_tiles(M, steps, sub, o, true, plan);
+                Plan tmp;
+                plan_tiles(M, steps, sub, o, true, &tmp);
+                close_tile_passes(M, steps, o, &tmp);
+                append_plan(tmp, plan);
             }
         }
     }
@@ -949,6 +1026,7 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
     tp.steps_in = plan->steps_in;
     tp.cancelled = plan->cancelled;
     plan_tiles(M, steps, order, oo, true, &tp);
+    close_tile_passes(M, steps, oo, &tp);
     double tcost = plan_cost_s(tp, M, oo.amp_bytes);
     {
         Plan cp;

@@ -421,12 +421,14 @@ int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L,
     return QSIM_OK;
 }
 
-int qsim_set_coset(qsim_ctx *c, int enable, int run_bits)
+int qsim_set_coset(qsim_ctx *c, int enable, int run_bits, int stage_kib)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
     if (run_bits < 0 || run_bits > 7) return fail(QSIM_EINVAL, "run_bits must be in [0, 7]");
+    if (stage_kib < 0 || stage_kib > 96) return fail(QSIM_EINVAL, "stage_kib must be in [0, 96]");
     c->opts.coset = enable != 0;
     c->opts.coset_run_bits = run_bits;
+    c->opts.coset_stage_kib = stage_kib;
     return QSIM_OK;
 }
 

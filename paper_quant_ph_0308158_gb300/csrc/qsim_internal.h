@@ -90,6 +90,8 @@ struct TilePass {
     uint32_t all_local; // 1 when no step has a control outside the tile
     uint32_t affine;    // 1 when every step has at most one control (NOT/CNOT)
     double touched;     // estimated fraction of tiles with an active step
+    double rebuilds;    // estimated permutation-table builds (tiles whose
+                        // active steps differ from the tile before)
     // Closed pass (qsim_jit_closed): the segment's net row map changes only
     // address bits inside the tile, so each tile holds every source of its
     // outputs; the segment's steps (Plan::jit_steps) are compiled in and
@@ -150,6 +152,7 @@ struct PlanOptions {
     bool closed_known = false;  // closed_delta holds the bits the circuit's net map changes
     uint64_t closed_delta = 0;
     int coset_run_bits = 0;  // r of those tiles (0: runs of 512 bytes)
+    int coset_stage_kib = 0; // pipeline stage of those passes (0: 32 KiB)
     int jit_min_steps = 32;  // shorter segments use the general kernel
 };
 

@@ -45,12 +45,15 @@ def test_mixed_circuit_is_one_gather(jit, variant):
 
 def test_hybrid_circuit_mixes_strategies_and_beats_both_pure_plans():
     cfg = W.config_hybrid()
-    for jit in (False, True):
+    # without compiled kernels the register part becomes a short interpreted
+    # gather; with them, passes over the register's tile that evaluate the
+    # compiled steps (closed passes: the register steps change only tile bits)
+    for jit, first in ((False, {"sliced"}), (True, {"closed"})):
         auto = _plan(cfg, jit=jit)
         gather = _plan(cfg, jit=jit, strategy="gather")
         tile = _plan(cfg, jit=jit, strategy="inplace")
         c = Counter(auto["variants"])
-        assert c["coset"] == 1 and c["tile"] >= 1 and len(c) == 2
+        assert c["coset"] == 1 and set(c) - {"coset"} == first
         assert auto["variants"][-1] == "coset"
         est = auto["stats"]["est_ms"]
         assert est < gather["stats"]["est_ms"] and est < tile["stats"]["est_ms"]
