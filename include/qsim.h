@@ -345,7 +345,19 @@ typedef struct qsim_batch_stats {
     double algorithmic_bytes; /* bytes read + written per run                */
     uint64_t arena_bytes;     /* device memory of the two state arenas       */
     void *stream;             /* cudaStream_t the batch runs on              */
+    uint64_t coset_passes;    /* NOT/CNOT gathers read in coset-tile order   */
+    uint64_t affine_passes;   /* NOT/CNOT gathers read row by row            */
+    uint64_t sliced_passes;   /* bit-sliced gathers of other segments        */
+    uint64_t sweep_passes;    /* in-place sweeps (steps beyond 8 controls)   */
 } qsim_batch_stats;
+
+/* Per-batch planning choices. */
+typedef struct qsim_batch_options {
+    uint32_t coset_min_qubits; /* NOT/CNOT circuits with M >= this read their
+                                  sources in coset-tile order (aligned runs);
+                                  smaller ones row by row (their states stay
+                                  in L2).  qsim_batch_create uses 18.      */
+} qsim_batch_options;
 
 /* Plan and allocate a batch.  M[i] in [1, QSIM_MAX_QUBITS]; steps[i] points to
  * L[i] steps (copied).  The states start zero-filled.  Device memory: two
@@ -353,6 +365,10 @@ typedef struct qsim_batch_stats {
  * circuit; QSIM_ENOMEM when the arenas do not fit. */
 int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *const *steps,
                       const size_t *L, qsim_batch **out);
+
+/* qsim_batch_create with planning options (opts NULL: the defaults). */
+int qsim_batch_create_ex(size_t n, const uint32_t *M, int dtype, const qsim_step *const *steps,
+                         const size_t *L, const qsim_batch_options *opts, qsim_batch **out);
 void qsim_batch_destroy(qsim_batch *b);
 
 /* Copy circuit i's state in from / out to host memory (n_amps = 2^M[i]);

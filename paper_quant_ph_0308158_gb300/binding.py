@@ -47,6 +47,7 @@ EXPORTS = (
     "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
     "qsim_set_wait_test", "qsim_set_coset", "qsim_gather_rows", "qsim_plan_circuit_ex",
+    "qsim_batch_create_ex",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
@@ -89,7 +90,9 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("circuits", ctypes.c_uint64), ("levels", ctypes.c_uint64),
                 ("items", ctypes.c_uint64), ("passes", ctypes.c_uint64),
                 ("amplitude_steps", ctypes.c_uint64), ("algorithmic_bytes", ctypes.c_double),
-                ("arena_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("arena_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("coset_passes", ctypes.c_uint64), ("affine_passes", ctypes.c_uint64),
+                ("sliced_passes", ctypes.c_uint64), ("sweep_passes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -109,6 +112,10 @@ class ServerStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("coset_min_qubits", ctypes.c_uint32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -178,6 +185,7 @@ def load() -> ctypes.CDLL:
             "qsim_load_state_async": ([p, p, sz], i),
             "qsim_probabilities_async": ([p, p, sz], i),
             "qsim_batch_create": ([sz, p, i, p, p, pp], i),
+            "qsim_batch_create_ex": ([sz, p, i, p, p, ctypes.POINTER(BatchOptions), pp], i),
             "qsim_batch_destroy": ([p], None),
             "qsim_batch_load_state": ([p, sz, p, sz], i),
             "qsim_batch_read_state": ([p, sz, p, sz], i),
@@ -500,7 +508,7 @@ class Batch:
     of persistent launches; ``run_plain()`` launches one kernel per circuit
     pass.  circuits: list of (M, steps)."""
 
-    def __init__(self, circuits, dtype=np.complex64):
+    def __init__(self, circuits, dtype=np.complex64, coset_min_qubits: int | None = None):
         self._lib = load()
         self.dtype = np.dtype(dtype)
         self.M = [int(m) for m, _ in circuits]
@@ -510,9 +518,10 @@ class Batch:
         ptrs = (ctypes.c_void_p * n)(*[s.ctypes.data if len(s) else 0 for s in self._steps])
         Ls = (ctypes.c_size_t * n)(*[len(s) for s in self._steps])
         self._b = ctypes.c_void_p()
-        _check(self._lib.qsim_batch_create(n, ctypes.cast(Ms, ctypes.c_void_p), dtype_code(self.dtype),
-                                           ctypes.cast(ptrs, ctypes.c_void_p),
-                                           ctypes.cast(Ls, ctypes.c_void_p), ctypes.byref(self._b)))
+        opts = None if coset_min_qubits is None else ctypes.byref(BatchOptions(coset_min_qubits))
+        _check(self._lib.qsim_batch_create_ex(n, ctypes.cast(Ms, ctypes.c_void_p), dtype_code(self.dtype),
+                                              ctypes.cast(ptrs, ctypes.c_void_p),
+                                              ctypes.cast(Ls, ctypes.c_void_p), opts, ctypes.byref(self._b)))
 
     def close(self):
         if self._b:

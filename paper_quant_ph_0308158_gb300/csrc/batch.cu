@@ -4,8 +4,10 @@
 // Every circuit of a batch owns a 2^M[i]-amplitude state inside one device
 // arena (plus a scratch arena of the same size for out-of-place gathers).
 // All circuits are planned once, at creation, with out-of-place gather
-// passes (GF(2) tables for NOT/CNOT runs, bit-sliced evaluation otherwise;
-// steps with more than eight controls as in-place sweeps).  Level p holds the
+// passes (GF(2) tables for NOT/CNOT runs -- read in coset-tile order for
+// states of at least coset_min_qubits, so that every DRAM burst is used in
+// full -- bit-sliced evaluation otherwise; steps with more than eight
+// controls as in-place sweeps).  Level p holds the
 // p-th pass of every circuit that has one; a level is one launch of
 // batch_kernel whose CTAs pull work items (16384 outputs of one pass) from a
 // counter.  The levels of a run are captured once into a CUDA graph and
@@ -67,6 +69,9 @@ struct qsim_batch {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t runs = 0;
+    uint32_t coset_min_qubits = 18;  // affine passes of larger states in coset-tile order
+    int *d_err = nullptr;            // error flag of the plain per-circuit launches
+    uint64_t coset_passes = 0, affine_passes = 0, sliced_passes = 0, sweep_passes = 0;
     double alg_bytes = 0;
     uint64_t steps_total = 0;
     uint64_t amp_steps = 0;
@@ -89,6 +94,7 @@ void batch_free(qsim_batch *b)
         if (b->arena[a]) cudaFree(b->arena[a]);
     if (b->d_tab) cudaFree(b->d_tab);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_err) cudaFree(b->d_err);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -134,6 +140,16 @@ int build_levels(qsim_batch *b, int r)
                 bp.out = a_in;  // in place
                 bp.sweep = p.sweep;
                 units = p.sweep.n_pairs;
+            } else if (p.gather.affine && p.gather.coset && b->M[i] >= b->coset_min_qubits) {
+                bp.kind = 7;
+                bp.in = a_in;
+                bp.out = a_out;
+                bp.bvec = p.gather.bvec;
+                bp.cr = p.gather.cr;
+                bp.cd = p.gather.cd;
+                bp.ctb = p.gather.ctb;
+                bp.tables = reinterpret_cast<const uint64_t *>(b->d_tab + b->tab_off[i]) + p.gather.coset_off;
+                cur[i] = 1 - cur[i];
             } else if (p.gather.affine) {
                 bp.kind = 3;
                 bp.in = a_in;
@@ -202,6 +218,12 @@ extern "C" {
 int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *const *steps,
                       const size_t *L, qsim_batch **out)
 {
+    return qsim_batch_create_ex(n, M, dtype, steps, L, nullptr, out);
+}
+
+int qsim_batch_create_ex(size_t n, const uint32_t *M, int dtype, const qsim_step *const *steps,
+                         const size_t *L, const qsim_batch_options *opts, qsim_batch **out)
+{
     if (!out) return bfail(QSIM_EINVAL, "out is NULL");
     *out = nullptr;
     const size_t amp = amp_of(dtype);
@@ -217,6 +239,7 @@ int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *c
     b->plans.resize(n);
     b->tab_off.resize(n);
     b->sl_off.resize(n);
+    if (opts) b->coset_min_qubits = opts->coset_min_qubits;
     uint64_t total = 0;
     size_t tab_bytes = 0;
     PlanOptions o;
@@ -224,7 +247,6 @@ int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *c
     o.scratch_available = true;
     o.strategy = QSIM_STRATEGY_GATHER;
     o.cancel_adjacent = false;
-    o.coset = false;  // affine passes run inside batch_kernel work items
     for (size_t i = 0; i < n; ++i) {
         std::string msg;
         int rc = make_plan(M[i], steps[i], L[i], o, &b->plans[i], &msg);
@@ -239,6 +261,10 @@ int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *c
         for (const Pass &p : b->plans[i].passes) {
             if (p.kind == kGather) ++g;
             b->alg_bytes += p.alg_bytes;
+            if (p.kind == kSweep) ++b->sweep_passes;
+            else if (!p.gather.affine) ++b->sliced_passes;
+            else if (p.gather.coset && M[i] >= b->coset_min_qubits) ++b->coset_passes;
+            else ++b->affine_passes;
         }
         b->gpass[i] = g;
         b->steps_total += L[i];
@@ -278,6 +304,8 @@ int qsim_batch_create(size_t n, const uint32_t *M, int dtype, const qsim_step *c
     size_t nlev = 0;
     for (const Plan &p : b->plans) nlev = std::max(nlev, p.passes.size());
     e = cudaMalloc(&b->d_counters, sizeof(uint32_t) * std::max<size_t>(1, nlev));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return fail_free(bfail(QSIM_ENOMEM, "batch counters"));
     for (int r = 0; r < 2 && rc == QSIM_OK; ++r) rc = build_levels(b, r);
     for (int r = 0; r < 2 && rc == QSIM_OK; ++r) rc = capture(b, r);
@@ -338,8 +366,9 @@ int qsim_batch_run_plain(qsim_batch *b)
             if (ps.kind == kSweep) {
                 e = launch_sweep(a_in, (int)b->amp, ps.sweep, nullptr, b->stream);
             } else {
-                e = launch_gather(a_in, a_out, (int)b->amp, b->M[i], ps.gather, tab, sl, nullptr, nullptr,
-                                  b->stream);
+                GatherPass g = ps.gather;
+                if (b->M[i] < b->coset_min_qubits) g.coset = 0;  // as in the batched plan
+                e = launch_gather(a_in, a_out, (int)b->amp, b->M[i], g, tab, sl, b->d_err, nullptr, b->stream);
                 cur = 1 - cur;
             }
             if (e != cudaSuccess)
@@ -369,6 +398,10 @@ int qsim_batch_info(qsim_batch *b, qsim_batch_stats *out)
     out->algorithmic_bytes = b->alg_bytes;
     out->arena_bytes = 2 * b->arena_bytes;
     out->stream = b->stream;
+    out->coset_passes = b->coset_passes;
+    out->affine_passes = b->affine_passes;
+    out->sliced_passes = b->sliced_passes;
+    out->sweep_passes = b->sweep_passes;
     return QSIM_OK;
 }
 

@@ -902,6 +902,53 @@ __device__ __forceinline__ void sweep_range(char *__restrict__ state, const Swee
 // batched execution: one persistent launch over the passes of many circuits
 // ============================================================================
 
+// Affine gather in coset-tile order: position p of the pass names local
+// output p mod 2^(r+d) of coset tile p >> (r+d) (see GatherPass).  A work
+// item covers whole tiles, so all reads of a tile's aligned source runs come
+// from one CTA within microseconds and every DRAM burst fetched is used in
+// full from L2, with no staging.
+template <int B>
+__device__ __forceinline__ void coset_order_range(const BatchPass &P, uint64_t p0, uint64_t p1,
+                                                  uint64_t step)
+{
+    using A = typename AmpOf<B>::T;
+    const A *src = reinterpret_cast<const A *>(P.in);
+    A *dst = reinterpret_cast<A *>(P.out);
+    const uint32_t rd = P.cr + P.cd;
+    const uint64_t low = (1ull << P.cr) - 1ull;
+    const uint64_t *tout = P.tables, *tsrc = P.tables + 256 * P.ctb;
+    const uint64_t *dstrun = P.tables + 512 * P.ctb, *srcrun = dstrun + (1u << P.cd);
+    const uint16_t *perm = reinterpret_cast<const uint16_t *>(srcrun + (1u << P.cd));
+    for (uint64_t q0 = p0; q0 < p1; q0 += 4 * step) {
+        A v[4];
+        uint64_t o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t q = q0 + u * step;
+            if (q < p1) {
+                const uint64_t t = q >> rd;
+                const uint32_t jj = (uint32_t)(q & ((1ull << rd) - 1ull));
+                uint64_t ob = 0, sb = P.bvec;
+                for (uint32_t k = 0; k < P.ctb; ++k) {
+                    const uint32_t b = (uint32_t)((t >> (8 * k)) & 255u);
+                    ob ^= __ldg(tout + 256 * k + b);
+                    sb ^= __ldg(tsrc + 256 * k + b);
+                }
+                const uint32_t loc = __ldg(perm + jj);
+                const uint64_t s = ((sb & ~low) ^ __ldg(srcrun + (loc >> P.cr))) | ((loc & low) ^ (sb & low));
+                o[u] = (ob ^ __ldg(dstrun + (jj >> P.cr))) | (jj & low);
+                v[u] = __ldg(src + s);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q0 + u * step < p1) {
+                if (dst) dst[o[u]] = v[u];
+                if (P.probs) P.probs[o[u]] = amp_prob(v[u]);
+            }
+    }
+}
+
 // CTAs take work items (a range of outputs of one circuit's pass) from a
 // global counter until the level's list is exhausted; the affine tables of
 // the last circuit served stay in shared memory.
@@ -938,6 +985,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchPass *__rest
             if (threadIdx.x == 0) s_tables = -1;
             sliced_chunk<B, WIDE, false, false>(P.in, P.out, P.M, o1, P.steps, P.nsteps, item.start, smem,
                                                 P.probs);
+        } else if (P.kind == 7) {
+            coset_order_range<B>(P, item.start + threadIdx.x, o1, kThreads);
         } else {
             sweep_range<B>(P.out, P.sweep, item.start + threadIdx.x, o1, kThreads);
         }

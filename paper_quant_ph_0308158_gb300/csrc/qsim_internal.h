@@ -181,13 +181,15 @@ struct BatchPass {
     const char *in;        // gather source (unused by sweeps)
     char *out;             // gather destination (NULL: probabilities only) / sweep state
     uint32_t M;
-    uint32_t kind;         // 1 sweep, 3 affine gather, 4 bit-sliced gather
+    uint32_t kind;         // 1 sweep, 3 affine gather, 4 bit-sliced gather,
+                           // 7 affine gather in coset-tile order
     uint32_t nbytes;       // affine: table bytes
     uint32_t nsteps;       // bit-sliced: steps
     uint64_t bvec;         // affine: constant term
-    const uint64_t *tables;       // affine tables (device)
+    const uint64_t *tables;       // affine tables (device); coset: the pass's coset tables
     const SlicedStep *steps;      // bit-sliced steps (device)
     double *probs;                // gathers: non-null = also write FP64 probabilities
+    uint32_t cr, cd, ctb, pad;    // coset: run bits, coset bits, tile-index bytes
     SweepParams sweep;
 };
 // A work item: outputs (or sweep pairs) [start, start + count) of one pass;

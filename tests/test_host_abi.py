@@ -50,7 +50,8 @@ def test_struct_layouts_match_the_binding(tmp_path):
     from paper_quant_ph_0308158_gb300 import binding as B
     structs = {"qsim_plan_stats": B.PlanStats, "qsim_batch_stats": B.BatchStats,
                "qsim_server_stats": B.ServerStats, "qsim_server_trace_record": B.ServerTraceRecord,
-               "qsim_tune_result": B.TuneResult, "qsim_plan_options": B.PlanOptions}
+               "qsim_tune_result": B.TuneResult, "qsim_plan_options": B.PlanOptions,
+               "qsim_batch_options": B.BatchOptions}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qsim.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
