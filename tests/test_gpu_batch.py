@@ -83,3 +83,34 @@ def test_batch_rejects_invalid_circuits():
     with pytest.raises(QsimError) as e:
         Batch([(4, W.cnot_circuit(4, 5, 1)), (4, bad)], np.complex64)
     assert "circuit 1" in str(e.value)
+
+
+@pytest.mark.parametrize("kind", ["cnot", "mixed"])
+@pytest.mark.parametrize("coset_min", [10, 18])
+def test_batch_at_workload_sizes_sampled(kind, coset_min):
+    """Circuits of the batched workload's sizes (M up to 22, L up to 2000,
+    complex64), NOT/CNOT circuits read in coset-tile order from M >=
+    coset_min: sampled rows of every circuit against the oracle's single-row
+    evaluation, after a graph run and after a plain run."""
+    rng = np.random.default_rng(44)
+    specs = [(22, 2000), (21, 1500), (20, 60), (18, 900), (17, 50), (14, 1200), (11, 700), (10, 50)]
+    circs = []
+    for i, (M, L) in enumerate(specs):
+        st = W.cnot_circuit(M, L, 4400 + i) if kind == "cnot" else W.mixed_circuit(M, L, 4400 + i)
+        circs.append((M, st))
+    states = [W.random_state(M, np.complex64, 900 + i) for i, (M, _) in enumerate(circs)]
+    with Batch(circs, np.complex64, coset_min_qubits=coset_min) as b:
+        info = b.info()
+        n_cnot_big = sum(1 for M, _ in specs if M >= coset_min) if kind == "cnot" else 0
+        assert info["coset_passes"] == n_cnot_big
+        for i, s in enumerate(states):
+            b.load_state(i, s)
+        for run in range(2):
+            b.run() if run == 0 else b.run_plain()
+            b.synchronize()
+            for i, (M, st) in enumerate(circs):
+                rows = rng.integers(0, 1 << M, size=min(1 << M, 1 << 14), dtype=np.uint64)
+                full = np.concatenate([st] * (run + 1))
+                src = oracle.source_rows(M, full, rows).astype(np.int64)
+                got = b.read_state(i)[rows.astype(np.int64)]
+                np.testing.assert_array_equal(got, states[i][src], err_msg="circuit %d run %d" % (i, run))
