@@ -9,7 +9,10 @@ the C ABI.
   lists and sweep pair enumeration, each evaluated on sampled rows against
   the circuit's own steps;
 - arena_check: the serving budget's first-fit allocator (coverage, no
-  overlap, merged free blocks, counters)."""
+  overlap, merged free blocks, counters);
+- prob_math_check: the complex64 probability arithmetic against the FPU;
+- closed_source_dump: the generated closed tile pass, evaluated on the host
+  and compiled with NVRTC."""
 import os
 import resource
 import subprocess
@@ -32,6 +35,18 @@ def test_planner_encodings(tmp_path, program):
                        preexec_fn=_limit_memory)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok:"), r.stdout
+
+
+def test_probability_arithmetic_matches_the_fpu(tmp_path):
+    """The complex64 probability, squared and summed in integer arithmetic
+    (prob_math.cuh compiled for the host), equals the host FPU's
+    (double)re*re + (double)im*im bit for bit on 28 million pairs: random
+    patterns, every exponent alignment of the add, and special values."""
+    exe = tmp_path / "prob_math_check"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", "native", "prob_math_check.cpp")], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("ok:"), r.stdout + r.stderr
 
 
 def test_c_program_builds_against_the_abi(tmp_path):
