@@ -99,16 +99,17 @@ def test_closed_pass_writes_probabilities(cuda, dtype):
         assert_probs_close(p.cpu().numpy(), want_p)
 
 
-def test_closed_pass_not_taken_when_every_bit_changes():
-    """A random circuit changes every bit: no closed pass, tile passes as
-    before, still exact."""
+def test_no_whole_circuit_closed_pass_when_every_bit_changes():
+    """A random circuit changes every bit: no single closed pass; its tile
+    segments (whose steps change only tile bits) may still run as closed
+    passes over their own tiles.  Exact either way."""
     M = 16
     steps = W.mixed_circuit(M, 200, 12)
     k1 = W.random_state(M, np.complex64, 12)
     want = oracle.apply_circuit(M, k1, steps).astype(np.complex64)
     got, kernels = _run_closed(M, np.complex64, steps, k1)
     np.testing.assert_array_equal(got, want)
-    assert "qsim_jit_closed" not in kernels
+    assert len(kernels) > 1
 
 
 def test_adder_m28_closed_full_state():

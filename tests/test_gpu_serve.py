@@ -170,3 +170,42 @@ def test_trace_records_each_request_in_order():
         assert len(srv.trace()) == 0  # moved out
         for rid in ids:
             srv.release(rid)
+
+
+def test_served_large_requests_alone_and_in_the_mix():
+    """Requests of the serving workload's larger sizes (M = 24, 26, 28:
+    states of 0.25-4 GiB, multi-GB device blocks and 64-bit offsets) mixed
+    with small ones: sampled probabilities against the oracle's single-row
+    evaluation, and each large result bit-identical when served alone."""
+    rng = np.random.default_rng(2428)
+    big = []
+    for i, (M, L) in enumerate([(24, 2600), (26, 1800), (28, 1200)]):
+        st = W.cnot_circuit(M, L, 8800 + i) if i != 1 else W.mixed_circuit(M, L, 8800 + i)
+        big.append((M, W.random_state(M, np.complex128, 8900 + i), st))
+    small = _requests(10, 5, 8, 16)
+    reqs = big[:1] + small[:5] + big[1:] + small[5:]
+    with Server(24 << 30, 8 << 30, np.complex128) as srv:
+        ids = [srv.submit(M, k1, st) for (M, k1, st) in reqs]
+        srv.wait_all(600)
+        assert srv.stats()["completed"] == len(reqs)
+        mixed = {}
+        for rid, (M, k1, st) in zip(ids, reqs):
+            done, _, p = srv.poll(rid)
+            assert done
+            if M >= 24:
+                rows = rng.integers(0, 1 << M, size=1 << 16, dtype=np.uint64)
+                rows[:2] = [0, (1 << M) - 1]
+                src = oracle.source_rows(M, st, rows).astype(np.int64)
+                assert_probs_close(p[rows.astype(np.int64)], oracle.probabilities(k1[src]))
+                mixed[M] = p.copy()
+            else:
+                assert_probs_close(p, _expected(M, k1, st))
+            srv.release(rid)
+    for M, k1, st in big:
+        with Server(24 << 30, 8 << 30, np.complex128) as srv:
+            r = srv.submit(M, k1, st)
+            srv.wait_all(300)
+            done, _, p = srv.poll(r)
+            assert done
+            np.testing.assert_array_equal(p, mixed[M])
+            srv.release(r)
