@@ -326,6 +326,7 @@ __device__ __forceinline__ void tr32(u32 (&a)[32])
 #define AB @B@
 #define BOX_BYTES @BOX@
 #define TABN ((NT * 33 + 7) / 8 * 8)  /* exchange-table entries, rounded to 16 bytes */
+#define STAGES @STAGES@
 __device__ __forceinline__ u64 tile_base(u64 t) { u64 b = 0; @TILEBASE@ return b; }
 __device__ __forceinline__ u64 deposit_high(u32 r) { u64 d = 0; @DEPHIGH@ return d; }
 __device__ __forceinline__ u64 deposit_rest(u32 r) { u64 d = 0; @DEPREST@ return d; }
@@ -333,16 +334,18 @@ extern "C" __global__ void __launch_bounds__(NT + 32, 1)
 qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap tmap)
 {
   extern __shared__ __align__(128) unsigned char smem[];
-  Amp *buf = reinterpret_cast<Amp *>(smem);
-  u64 *depo = reinterpret_cast<u64 *>(smem + ((size_t)AB << K));
+  Amp *bufs = reinterpret_cast<Amp *>(smem);
+  u64 *depo = reinterpret_cast<u64 *>(smem + ((size_t)AB << K) * STAGES);
   u16 *tabs = reinterpret_cast<u16 *>(depo + (1u << NH));
   u64 *full = reinterpret_cast<u64 *>(tabs + TABN);
-  u64 *empty = full + 1;
+  u64 *empty = full + STAGES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (u32 r = tid; r < (1u << NH); r += NT + 32) depo[r] = deposit_high(r);
   if (tid == 0) {
-    mbar_init(full, 1);
-    mbar_init(empty, NT / 32);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NT / 32);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -350,21 +353,23 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
   const u64 begin = (u64)blockIdx.x * per;
   const u64 end = begin + per < p.n_tiles ? begin + per : p.n_tiles;
   if (warp == NT / 32) {
-    // producer warp: one tile per phase of the single stage
+    // producer warp: tile it goes to stage it % STAGES once that stage's
+    // previous tile has been consumed
     for (u64 t = begin; t < end; ++t) {
-      const u32 it = (u32)(t - begin);
-      if (it >= 1 && !mbar_wait(empty, (it - 1) & 1u, p.wait_limit)) {
+      const u32 it = (u32)(t - begin), s = it % STAGES;
+      if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1u, p.wait_limit)) {
         if (lane == 0) atomicOr(p.err, 2);
         return;
       }
       const u64 base = tile_base(t);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (lane == 0) mbar_expect(full, (u32)((size_t)AB << K));
+      if (lane == 0) mbar_expect(&full[s], (u32)((size_t)AB << K));
       __syncwarp();
+      char *buf = reinterpret_cast<char *>(bufs) + ((size_t)AB << K) * s;
       for (u32 r = lane; r < (1u << NREST); r += 32) {
         const u64 g = base | deposit_rest(r);
         @COORDS@
-        tma5(reinterpret_cast<char *>(buf) + (size_t)r * BOX_BYTES, &tmap, c0, c1, c2, c3, c4, full);
+        tma5(buf + (size_t)r * BOX_BYTES, &tmap, c0, c1, c2, c3, c4, &full[s]);
       }
     }
     return;
@@ -373,7 +378,7 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
   // shared memory to global memory in coalesced runs
   u16 *tab = tabs + warp * 32 * 33;
   for (u64 t = begin; t < end; ++t) {
-    const u32 it = (u32)(t - begin);
+    const u32 it = (u32)(t - begin), s = it % STAGES;
     const u64 base = tile_base(t);
     {
       const u32 j0 = (u32)tid * 32u;
@@ -388,10 +393,11 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
       for (int u = 0; u < 32; ++u) tab[lane * 33 + u] = (u16)r[u];
       __syncwarp();
     }
-    if (!mbar_wait(full, it & 1u, p.wait_limit)) {
+    if (!mbar_wait(&full[s], (it / STAGES) & 1u, p.wait_limit)) {
       if (tid == 0) atomicOr(p.err, 1);
       return;
     }
+    const Amp *buf = bufs + ((size_t)1 << K) * s;
 #pragma unroll 1
     for (int e0 = 0; e0 < 32; e0 += 8) {
       Amp v[8];
@@ -409,7 +415,7 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(empty);
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 )QSIMSRC";
@@ -428,6 +434,18 @@ std::vector<uint32_t> tile_local_bits(const TilePass &t)
     for (uint32_t q = 0; q < t.l; ++q) lb.push_back(q);
     for (uint32_t q = 0; q < t.nh; ++q) lb.push_back(t.high[q]);
     return lb;
+}
+
+// Pipeline stages of a closed pass: as many tiles as fit next to the
+// exchange tables and the deposit table in 220 KiB of shared memory, at most 4.
+uint32_t closed_stages(int amp, const TilePass &t)
+{
+    const size_t nt = ((size_t)1 << t.k) / 32;
+    const size_t fixed = 2 * ((nt * 33 + 7) / 8 * 8) + sizeof(uint64_t) * ((size_t)1 << t.nh) + 64;
+    const size_t tile = (size_t)amp << t.k;
+    size_t st = (220 * 1024 - fixed) / (tile + 16);
+    if (st > 4) st = 4;
+    return st < 1 ? 1 : (uint32_t)st;
 }
 
 std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
@@ -478,6 +496,7 @@ std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, 
     replace_all(src, "@NT@", std::to_string((1u << K) / 32));
     replace_all(src, "@B@", std::to_string(amp));
     replace_all(src, "@BOX@", std::to_string(t.box_bytes));
+    replace_all(src, "@STAGES@", std::to_string(closed_stages(amp, t)));
     replace_all(src, "@TILEBASE@", tb.str());
     replace_all(src, "@DEPHIGH@", dh.str());
     replace_all(src, "@DEPREST@", dr.str());
@@ -675,7 +694,9 @@ size_t closed_smem_bytes(int amp, const TilePass &t)
 {
     const size_t nt = ((size_t)1 << t.k) / 32;
     const size_t tabn = (nt * 33 + 7) / 8 * 8;
-    return ((size_t)amp << t.k) + sizeof(uint64_t) * ((size_t)1 << t.nh) + 2 * tabn + 2 * sizeof(uint64_t);
+    const size_t st = closed_stages(amp, t);
+    return ((size_t)amp << t.k) * st + sizeof(uint64_t) * ((size_t)1 << t.nh) + 2 * tabn +
+           2 * sizeof(uint64_t) * st;
 }
 
 int closed_get(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t, JitEntry **e,

@@ -943,7 +943,8 @@ bool plan_closed(uint32_t M, const qsim_step *steps, const std::vector<uint64_t>
                  const PlanOptions &o, Plan *plan)
 {
     if (!o.jit || !o.closed_known || order.empty()) return false;
-    const uint32_t kmax = std::min<uint32_t>(o.amp_bytes == 16 ? 13 : 14, M);
+    uint32_t kmax = std::min<uint32_t>(o.amp_bytes == 16 ? 13 : 14, M);
+    if (o.tile_bits > 0) kmax = std::min<uint32_t>(kmax, (uint32_t)o.tile_bits);
     uint64_t T = o.closed_delta & full_mask(M);
     if ((uint32_t)popcount64(T) > kmax) return false;
     for (uint32_t b = 0; b < M && (uint32_t)popcount64(T) < kmax; ++b) T |= 1ull << b;
