@@ -969,6 +969,8 @@ def run_serve(args, rank, ws, local):
     srv = Server(budget, host_bytes, dtype)
     srv.set_backfill(args.serve_backfill_ms)
     srv.set_copy_streams(args.serve_copy_streams)
+    if args.serve_upload_chunk_mb:
+        srv.set_upload_chunk(args.serve_upload_chunk_mb << 20)
     if args.serve_trace:
         srv.set_tracing(True)
     lat = []
@@ -1000,10 +1002,26 @@ def run_serve(args, rank, ws, local):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     st = srv.stats()
+    uploads = None
     if args.serve_trace:
         tr = srv.trace()
         np.savetxt(args.serve_trace, np.column_stack([tr[f] for f in tr.dtype.names]),
                    delimiter=",", header=",".join(tr.dtype.names), comments="", fmt="%.6g")
+        # per-copy rates of the state uploads: by request size and over time
+        dur = tr["upload_end_ms"] - tr["upload_start_ms"]
+        ok = dur > 0
+        gbs = (16.0 * np.exp2(tr["M"][ok].astype(np.float64))) / dur[ok] / 1e6
+        ms = tr["M"][ok]
+        t_mid = 0.5 * (tr["upload_start_ms"][ok] + tr["upload_end_ms"][ok])
+        uploads = {"by_M_median_gbs": {int(m): float(np.median(gbs[ms == m])) for m in np.unique(ms)},
+                   "p10_p50_p90_gbs": [float(np.percentile(gbs, q)) for q in (10, 50, 90)]}
+        if len(t_mid):
+            edges = np.linspace(t_mid.min(), t_mid.max() + 1e-9, 11)
+            idx = np.digitize(t_mid, edges) - 1
+            big = ms >= 26
+            uploads["M26plus_median_gbs_by_tenth_of_run"] = [
+                float(np.median(gbs[(idx == b) & big])) if np.any((idx == b) & big) else None
+                for b in range(10)]
     srv.close()
     lat_a = np.array(lat)
     value = amp_steps / wall
@@ -1024,6 +1042,7 @@ def run_serve(args, rank, ws, local):
                    "rounds": st["rounds"], "peak_hbm_in_use": st["peak_in_use_bytes"],
                    "backfill_ms": args.serve_backfill_ms, "backfilled": st["backfilled"],
                    "copy_streams": args.serve_copy_streams,
+                   "upload_chunk_mb": args.serve_upload_chunk_mb, "uploads": uploads,
                    "h2d_gbs_while_busy": st["h2d_bytes"] / max(st["h2d_busy_ms"], 1e-9) / 1e6,
                    "d2h_gbs_while_busy": st["d2h_bytes"] / max(st["d2h_busy_ms"], 1e-9) / 1e6,
                    "h2d_busy_frac": st["h2d_busy_ms"] / (1e3 * wall),
@@ -1062,6 +1081,8 @@ def main():
     ap.add_argument("--serve-host-gb", type=float, default=48.0)
     ap.add_argument("--serve-backfill-ms", type=float, default=100.0,
                     help="admit later requests ahead of a head that waited less (-1: FIFO)")
+    ap.add_argument("--serve-upload-chunk-mb", type=int, default=0,
+                    help="upload each state in copies of this many MiB (0: one copy)")
     ap.add_argument("--serve-copy-streams", type=int, default=2, choices=[1, 2],
                     help="copies in and out on two overlapping streams or on one")
     ap.add_argument("--serve-trace", default="",

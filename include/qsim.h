@@ -476,6 +476,11 @@ int qsim_server_set_backfill(qsim_server *s, double max_head_wait_ms);
  * stream (n = 1).  QSIM_EBUSY while requests are running. */
 int qsim_server_set_copy_streams(qsim_server *s, int n);
 
+/* Upload each admitted state in copies of at most bytes (0, the default: one
+ * copy per state); bytes must be 0 or at least 1 MiB and a multiple of 256
+ * (QSIM_EINVAL otherwise).  Applies to requests admitted afterwards. */
+int qsim_server_set_upload_chunk(qsim_server *s, size_t bytes);
+
 /* Pause (paused != 0) or resume admission.  While paused, submitted requests
  * wait and admitted ones run to completion; e.g. to submit a group of
  * requests that should be admitted together. */

@@ -58,7 +58,7 @@ EXPORTS = (
     "qsim_server_submit", "qsim_server_poll", "qsim_server_release", "qsim_server_wait_all",
     "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain", "qsim_server_set_backfill",
     "qsim_server_set_paused", "qsim_server_set_tracing", "qsim_server_get_trace",
-    "qsim_server_set_copy_streams",
+    "qsim_server_set_copy_streams", "qsim_server_set_upload_chunk",
 )
 
 
@@ -205,6 +205,7 @@ def load() -> ctypes.CDLL:
             "qsim_server_set_backfill": ([p, ctypes.c_double], i),
             "qsim_server_set_paused": ([p, i], i),
             "qsim_server_set_copy_streams": ([p, i], i),
+            "qsim_server_set_upload_chunk": ([p, sz], i),
             "qsim_server_set_tracing": ([p, i], i),
             "qsim_server_get_trace": ([p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_server_destroy": ([p], None),
@@ -605,6 +606,9 @@ class Server:
     def set_copy_streams(self, n: int):
         """Copies in and out on two overlapping streams (2) or one stream (1)."""
         _check(self._lib.qsim_server_set_copy_streams(self._s, int(n)))
+
+    def set_upload_chunk(self, nbytes: int):
+        _check(self._lib.qsim_server_set_upload_chunk(self._s, nbytes))
 
     def set_paused(self, paused: bool):
         """Pause or resume admission (admitted requests keep running)."""

@@ -107,6 +107,7 @@ struct qsim_server {
     double max_head_wait_ms = 100.0;  // backfill admission while the head waited less
     size_t pending_upload_bytes = 0;  // admitted states not yet on the device
     int copy_streams = 2;             // 2: copies in and out overlap; 1: one copy stream
+    size_t upload_chunk = 0;          // state uploads in copies of at most this many bytes (0: one)
     cudaEvent_t t0_event = nullptr;   // device-time origin of the trace
     Clock::time_point t0;             // host-time origin of the trace
     bool tracing = false;
@@ -225,7 +226,13 @@ Admit try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
     cudaError_t e = cudaEventRecord(r->up0, s->h2d);
     if (e != cudaSuccess) return fail_admission(s, r, "cudaEventRecord(upload start)", e);
     const auto e0 = Clock::now();
-    e = cudaMemcpyAsync(r->buf[0], r->host_in, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
+    {
+        const size_t total = n * s->amp;
+        const size_t chunk = s->upload_chunk ? s->upload_chunk : total;
+        for (size_t off = 0; off < total && e == cudaSuccess; off += chunk)
+            e = cudaMemcpyAsync(r->buf[0] + off, static_cast<const char *>(r->host_in) + off,
+                                std::min(chunk, total - off), cudaMemcpyHostToDevice, s->h2d);
+    }
     if (e != cudaSuccess) return fail_admission(s, r, "cudaMemcpyAsync(state upload)", e);
     if (tb) {
         e = cudaMemcpyAsync(r->d_tab, h_tab, tb, cudaMemcpyHostToDevice, s->h2d);
@@ -707,6 +714,15 @@ int qsim_server_get_trace(qsim_server *s, qsim_server_trace_record *out, size_t 
     if (n) std::memcpy(out, s->trace.data(), n * sizeof(qsim_server_trace_record));
     s->trace.erase(s->trace.begin(), s->trace.begin() + (std::ptrdiff_t)n);
     *n_out = n;
+    return QSIM_OK;
+}
+
+int qsim_server_set_upload_chunk(qsim_server *s, size_t bytes)
+{
+    if (!s) return sfail(QSIM_EINVAL, "NULL argument");
+    if (bytes && (bytes < (1u << 20) || bytes % 256)) return sfail(QSIM_EINVAL, "chunk must be 0 or >= 1 MiB, a multiple of 256");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->upload_chunk = bytes;
     return QSIM_OK;
 }
 
