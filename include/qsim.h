@@ -247,7 +247,7 @@ int qsim_jit_precompile(uint32_t M, int dtype, const qsim_step *steps, size_t L,
 /* Affine (NOT/CNOT-only) gather segments, x(i) = A i ^ b over GF(2) (the
  * Sec. 2h product of such steps): with enable = 1 (default) they run as
  * coset-blocked tiles, whose reads and writes are aligned runs of 2^run_bits
- * amplitudes (run_bits 0: runs of 512 bytes; at most 7), moved through a
+ * amplitudes (run_bits 0: runs of 1 KiB; at most 7), moved through a
  * pipeline whose stages hold at least stage_kib KiB of tiles (0: 32; at most
  * 96); with enable = 0 each output reads its source directly (scattered
  * reads).  Results are identical.  QSIM_EINVAL for run_bits outside [0, 7] or

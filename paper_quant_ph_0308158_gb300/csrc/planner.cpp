@@ -456,7 +456,7 @@ bool emit_coset(uint32_t M, const uint64_t *col, uint64_t bvec, const PlanOption
 {
     (void)bvec;
     const uint32_t amp = (uint32_t)o.amp_bytes;
-    uint32_t r = o.coset_run_bits > 0 ? (uint32_t)o.coset_run_bits : (amp == 16 ? 5u : 6u);
+    uint32_t r = o.coset_run_bits > 0 ? (uint32_t)o.coset_run_bits : (amp == 16 ? 6u : 7u);  // 1 KiB runs
     r = std::min(std::min(r, 7u), M);  // local indices (r + d <= 14 bits) fit 16 bits
     const size_t keep = plan->gather_tables.size();
     for (; r >= 1; --r) {

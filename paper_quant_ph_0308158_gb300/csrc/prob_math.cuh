@@ -16,14 +16,13 @@
 // leading bit at bit 52 after shifting P left by 52 - lead(P).  Zero squares
 // to +0, infinity to infinity, NaN to a quiet NaN.  This keeps conversions
 // and multiplies off the FP64 pipe (its issue rate, not HBM, bounds an FP64
-// evaluation on GB300).  Normal numbers and zeros take a short inlined path
-// (the significand square is normalised by a shift of (P << 6) >> (P >> 47))
-// and are summed in integer arithmetic too: both squares are non-negative
-// zeros or normal doubles (a float's square is never a double subnormal),
-// so the sum aligns the smaller significand with eight guard bits and a
-// sticky bit, renormalises once and rounds to nearest-even -- the one
-// rounding of an FP64 add, bit for bit.  The rest (subnormal, infinite or NaN
-// floats) take an out-of-line general path whose sum is the FP64 add.
+// evaluation on GB300): the one FP64 instruction is the sum, whose rounding
+// is the only one, so the result equals squaring and adding in FP64.  (A sum
+// in integer arithmetic as well -- align, guard and sticky bits, round to
+// nearest-even -- was measured slower: about 80 integer instructions cost
+// more issue slots than one FP64 add.)  Normal numbers and zeros take a
+// short inlined path (the significand square is normalised by a shift of
+// (P << 6) >> (P >> 47)); the rest an out-of-line general one.
 //
 // complex128: im^2 rounded, then one fused multiply-add -- within one unit in
 // the last place of two separately rounded products.
@@ -57,37 +56,12 @@
     {                                                                                       \
         return (((u >> 23) & 0xFFu) - 1u) < 254u || (u << 1) == 0u;                         \
     }                                                                                       \
-    Q unsigned long long qsim_add_sq_bits(unsigned long long x, unsigned long long y)       \
-    {                                                                                       \
-        const unsigned long long hi = x > y ? x : y, lo = x > y ? y : x;                    \
-        const unsigned int eh = (unsigned int)(hi >> 52), el = (unsigned int)(lo >> 52);    \
-        const unsigned int d = eh - el;                                                     \
-        if (el == 0u || d > 53u) return hi;                                                 \
-        const unsigned long long one = 1ull << 52, frac = one - 1ull;                       \
-        const unsigned long long bs = ((lo & frac) | one) << 8;                             \
-        unsigned long long sum = (((hi & frac) | one) << 8) + (bs >> d);                    \
-        unsigned long long sticky = (bs & ((1ull << d) - 1ull)) != 0ull;                    \
-        unsigned long long ex = eh;                                                         \
-        if (sum >> 61) {                                                                    \
-            sticky |= sum & 1ull;                                                           \
-            sum >>= 1;                                                                      \
-            ++ex;                                                                           \
-        }                                                                                   \
-        const unsigned long long rem = sum & 0xFFull;                                       \
-        unsigned long long m = sum >> 8;                                                    \
-        m += (rem > 0x80ull) || (rem == 0x80ull && (sticky || (m & 1ull)));                 \
-        if (m >> 53) {                                                                      \
-            m >>= 1;                                                                        \
-            ++ex;                                                                           \
-        }                                                                                   \
-        return (ex << 52) | (m & frac);                                                     \
-    }                                                                                       \
     Q double qsim_prob_c64(float re, float im)                                              \
     {                                                                                       \
         const unsigned int a = __float_as_uint(re), b = __float_as_uint(im);                \
         if (qsim_square_fast_ok(a) && qsim_square_fast_ok(b))                               \
-            return __longlong_as_double((long long)qsim_add_sq_bits(qsim_square_bits_fast(a), \
-                                                                     qsim_square_bits_fast(b))); \
+            return __dadd_rn(__longlong_as_double((long long)qsim_square_bits_fast(a)),     \
+                             __longlong_as_double((long long)qsim_square_bits_fast(b)));    \
         return __dadd_rn(__longlong_as_double((long long)qsim_square_bits(a)),              \
                          __longlong_as_double((long long)qsim_square_bits(b)));             \
     }                                                                                       \

@@ -151,7 +151,7 @@ struct PlanOptions {
     bool coset = true;       // affine segments through coset-blocked tiles
     bool closed_known = false;  // closed_delta holds the bits the circuit's net map changes
     uint64_t closed_delta = 0;
-    int coset_run_bits = 0;  // r of those tiles (0: runs of 512 bytes)
+    int coset_run_bits = 0;  // r of those tiles (0: runs of 1 KiB)
     int coset_stage_kib = 0; // pipeline stage of those passes (0: 32 KiB)
     int jit_min_steps = 32;  // shorter segments use the general kernel
 };

@@ -1,10 +1,10 @@
 // Host check of the probability arithmetic (built and run by
 // tests/test_native_checks.py, no GPU).  prob_math.cuh is compiled as host
 // C++ with host stand-ins for the few CUDA intrinsics it names; for complex64
-// inputs its result must equal (double)re*re + (double)im*im computed by the
-// host FPU (each square exact, one round-to-nearest-even add), bit for bit,
-// on random values over the whole exponent range, on pairs chosen to make
-// the add round at every alignment, and on special values.
+// inputs its result (squares built exactly in integer arithmetic, one FP64
+// add) must equal (double)re*re + (double)im*im computed by the host FPU,
+// bit for bit, on random values over the whole exponent range, on pairs
+// chosen to make the add round at every alignment, and on special values.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>

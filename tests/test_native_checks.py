@@ -38,8 +38,9 @@ def test_planner_encodings(tmp_path, program):
 
 
 def test_probability_arithmetic_matches_the_fpu(tmp_path):
-    """The complex64 probability, squared and summed in integer arithmetic
-    (prob_math.cuh compiled for the host), equals the host FPU's
+    """The complex64 probability, squared exactly in integer arithmetic and
+    summed by one FP64 add (prob_math.cuh compiled for the host), equals the
+    host FPU's
     (double)re*re + (double)im*im bit for bit on 28 million pairs: random
     patterns, every exponent alignment of the add, and special values."""
     exe = tmp_path / "prob_math_check"
