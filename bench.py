@@ -398,7 +398,9 @@ def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, s
         tuned = {"seconds": time.perf_counter() - t0, "chosen": cands[0], "candidates": cands}
 
     def step():
-        if args.separate_probs:
+        if qubits is not None:  # App. 1 input generated within the step (first pass)
+            sim.apply_product(qubits, steps, probs.data_ptr())
+        elif args.separate_probs:
             sim.apply(steps)
             sim.probabilities_device(probs.data_ptr())
         else:

@@ -133,6 +133,20 @@ int qsim_load_state(qsim_ctx *ctx, const void *host_amps, size_t n_amps);
  * stream; qubits is copied during the call. */
 int qsim_load_product_state(qsim_ctx *ctx, const double *qubits);
 
+/* Apply a circuit to the product state of App. 1 (qubits as for
+ * qsim_load_product_state) without writing that state out first: when the
+ * plan's first pass is a tile pass, it computes every source amplitude from
+ * the qubits instead of loading it -- the product over the tile's outside
+ * bits once per tile, over its high bits per tile for each of their values,
+ * over its low bits once per pass, all in FP64; for complex64 the per-output
+ * product of the last two is taken in float-float arithmetic (about 48
+ * significant bits) and rounded once, for complex128 in FP64.  Other plans
+ * start from qsim_load_product_state.  The context's state is overwritten.
+ * d_probs NULL: no probabilities; else as qsim_apply_circuit_probabilities.
+ * Errors as qsim_apply_circuit. */
+int qsim_apply_circuit_product(qsim_ctx *ctx, const double *qubits, const qsim_step *steps, size_t L,
+                               double *d_probs);
+
 /* Copy the state (k2) to host memory; n_amps must equal 2^M.  Waits for all
  * work queued on the context and reports device-side errors. */
 int qsim_read_state(qsim_ctx *ctx, void *host_amps, size_t n_amps);

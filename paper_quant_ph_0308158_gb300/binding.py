@@ -47,7 +47,7 @@ EXPORTS = (
     "qsim_set_strategy",
     "qsim_set_canonicalize", "qsim_set_profiling", "qsim_get_pass_times", "qsim_set_jit",
     "qsim_set_wait_test", "qsim_set_coset", "qsim_gather_rows", "qsim_plan_circuit_ex",
-    "qsim_batch_create_ex",
+    "qsim_batch_create_ex", "qsim_apply_circuit_product",
     "qsim_jit_precompile",
     "qsim_get_plan_stats", "qsim_synchronize", "qsim_probabilities",
     "qsim_probabilities_device", "qsim_plan_circuit", "qsim_last_error", "qsim_version",
@@ -169,6 +169,7 @@ def load() -> ctypes.CDLL:
             "qsim_set_jit": ([p, i], i),
             "qsim_set_wait_test": ([p, u32], i),
             "qsim_set_coset": ([p, i, i, i], i),
+            "qsim_apply_circuit_product": ([p, p, p, sz, p], i),
             "qsim_gather_rows": ([p, p, p, u32, i, p, i, p], i),
             "qsim_plan_circuit_ex": ([u32, i, p, sz, ctypes.POINTER(PlanOptions), ctypes.POINTER(PlanStats),
                                       p, p, p, p, sz], i),
@@ -415,6 +416,17 @@ class Simulator:
     def apply(self, steps):
         s = as_steps(steps)
         _check(self._lib.qsim_apply_circuit(self._ctx, _ptr(s), len(s)))
+
+    def apply_product(self, qubits: np.ndarray, steps, out_ptr: int = 0):
+        """Apply steps to the App. 1 product state of qubits (M x 2 complex),
+        the first tile pass computing its inputs (probabilities to out_ptr if
+        non-zero)."""
+        q = np.ascontiguousarray(qubits, dtype=np.complex128)
+        if q.shape != (self.M, 2):
+            raise QsimError(QSIM_EINVAL, "qubits must be a complex (M, 2) array")
+        s = as_steps(steps)
+        _check(self._lib.qsim_apply_circuit_product(self._ctx, _ptr(q), _ptr(s), len(s),
+                                                    ctypes.c_void_p(out_ptr or None)))
 
     def apply_probabilities(self, steps, out_ptr: int):
         """apply(steps), then FP64 probabilities into device memory at out_ptr

@@ -198,6 +198,11 @@ struct TileKParams {
     uint32_t rest_pos[kMaxHighBits];
     uint32_t wait_limit;           // polls before a pipeline wait gives up
     uint32_t stall_producer;       // testing: the producer leaves without loading a tile
+    // App. 1 input (product-input pass): source amplitudes are computed, not
+    // loaded.  qtab: per address bit b, (q_b(0), q_b(1)) as FP64 complex;
+    // plow: the product over the tile's low l bits for each of their 2^l
+    // values; phigh: over its high bits for each of their 2^nh values.
+    const double2 *qtab, *plow, *phigh;
 };
 
 struct TileStageMeta {
@@ -241,7 +246,71 @@ __device__ __forceinline__ void consumer_sync()
 // producer finds the CTA's next tile with an active step, publishes its
 // base and active-step mask in the stage's metadata, and issues one bulk
 // copy per contiguous run of 2^l amplitudes; an empty tile marks the end.
-template <int B, bool PROBS>
+// Float-float complex number (each part an unevaluated sum hi + lo of two
+// floats, about 48 significant bits): the product-input pass multiplies in it
+// so that complex64 amplitudes cost FP32 work, not FP64 issue.
+struct FFc {
+    float rh, rl, ih, il;
+};
+
+__device__ __forceinline__ FFc ffc_of(double2 v)
+{
+    FFc r;
+    r.rh = __double2float_rn(v.x);
+    r.rl = __double2float_rn(v.x - (double)r.rh);
+    r.ih = __double2float_rn(v.y);
+    r.il = __double2float_rn(v.y - (double)r.ih);
+    return r;
+}
+
+// x*y + sign*z*w in float-float (error-free products by fma, Dekker/Knuth
+// two-sum for the high parts), rounded to one float at the end.
+__device__ __forceinline__ float ff_dot2_round(float xh, float xl, float yh, float yl, float zh, float zl,
+                                               float wh, float wl, float sign)
+{
+    const float p1 = xh * yh;
+    const float e1 = fmaf(xh, yh, -p1);
+    const float p2 = sign * zh * wh;
+    const float e2 = fmaf(sign * zh, wh, -p2);
+    const float s = p1 + p2;  // two-sum of the high products
+    const float bb = s - p1;
+    const float err = (p1 - (s - bb)) + (p2 - bb);
+    const float cross = fmaf(xh, yl, xl * yh) + sign * fmaf(zh, wl, zl * wh);
+    return s + (err + e1 + e2 + cross);
+}
+
+__device__ __forceinline__ double2 dcmul(double2 a, double2 b)
+{
+    return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
+                        __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+
+// Partial products of the product-input pass kept per tile: float-float for
+// complex64 output, FP64 for complex128.
+template <int B> struct ProdT;
+template <> struct ProdT<8> {
+    using T = FFc;
+    static __device__ __forceinline__ T of(double2 v) { return ffc_of(v); }
+    static __device__ __forceinline__ uint2 mul(const T &a, const T &b)
+    {
+        const float re = ff_dot2_round(a.rh, a.rl, b.rh, b.rl, a.ih, a.il, b.ih, b.il, -1.0f);
+        const float im = ff_dot2_round(a.rh, a.rl, b.ih, b.il, a.ih, a.il, b.rh, b.rl, 1.0f);
+        return make_uint2(__float_as_uint(re), __float_as_uint(im));
+    }
+};
+template <> struct ProdT<16> {
+    using T = double2;
+    static __device__ __forceinline__ T of(double2 v) { return v; }
+    static __device__ __forceinline__ uint4 mul(const T &a, const T &b)
+    {
+        const double2 v = dcmul(a, b);
+        const unsigned long long x = (unsigned long long)__double_as_longlong(v.x);
+        const unsigned long long y = (unsigned long long)__double_as_longlong(v.y);
+        return make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)y, (uint32_t)(y >> 32));
+    }
+};
+
+template <int B, bool PROBS, bool PRODUCT>
 __global__ void __launch_bounds__(kTileThreads + 32, 1)
     tile_kernel(TileKParams p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -311,7 +380,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                     mask[w] = __ballot_sync(0xffffffffu, act);
                     any |= mask[w] != 0;
                 }
-                if (any || PROBS) break;  // a pass that writes probabilities visits every tile
+                if (any || PROBS || PRODUCT) break;  // these passes write every tile
                 base = kNoTile;
             }
             bool same = have_last && base != kNoTile;
@@ -332,6 +401,10 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
             if (base == kNoTile) {
                 if (lane == 0) mbar_arrive(&full[s]);  // end marker, no bytes
                 return;
+            }
+            if (PRODUCT) {  // nothing to load: the consumers compute the sources
+                if (lane == 0) mbar_arrive(&full[s]);
+                continue;
             }
             fence_proxy_async_smem();
             if (lane == 0) mbar_arrive_expect_tx(&full[s], run_bytes << p.nh);
@@ -366,6 +439,14 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     bool have_perm = false;  // perm holds the table of an earlier tile
     uint32_t c0 = 0, delta = 0;  // affine passes: image of 0 in that table, shift now
     A *st = reinterpret_cast<A *>(p.state);
+    // product input: the tile buffers are free, so they hold the per-tile
+    // products over the high bits (2^nh) and the products over the low bits
+    using PT = typename ProdT<B>::T;
+    PT *thigh = reinterpret_cast<PT *>(bufs);
+    PT *tlow = thigh + (1u << p.nh);
+    if (PRODUCT) {
+        for (uint32_t u = tid; u < (1u << p.l); u += kTileThreads) tlow[u] = ProdT<B>::of(p.plow[u]);
+    }
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
         if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u, p.wait_limit)) {
@@ -374,10 +455,12 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
         }
         const uint64_t base = meta[s].base;
         if (base == kNoTile) break;
-        bool idle = PROBS;  // no active step: only a pass writing probabilities sends such a tile
+        // no active step: only a pass writing probabilities or product input
+        // sends such a tile
+        bool idle = PROBS || PRODUCT;
 #pragma unroll
         for (int w = 0; w < kMaskWords; ++w) idle = idle && meta[s].mask[w] == 0u;
-        if (PROBS && idle) {
+        if (PROBS && !PRODUCT && idle) {
             const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
             for (uint32_t j = tid; j < tile_amps; j += kTileThreads)
                 p.probs[base + depo[j >> p.l] + (j & lmask)] = amp_prob(buf[j]);
@@ -385,7 +468,9 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
             if (lane == 0) mbar_arrive(&empty[s]);
             continue;
         }
-        if (!meta[s].same && p.affine && have_perm) {
+        if (idle) {
+            // product input, no active step: every output is its own source
+        } else if (!meta[s].same && p.affine && have_perm) {
             // NOT/CNOT segment: every tile's map is A j ^ c(tile) with the same
             // A, so the table of the first tile is reused with c(tile) ^ c(first)
             uint32_t c = 0;
@@ -423,13 +508,42 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
             have_perm = true;
             consumer_sync();  // the new table is complete
         }
+        if (PRODUCT) {
+            // this tile's factor over the bits outside it (a butterfly product
+            // over the lanes of each warp; every warp gets the same value),
+            // then its products over the high tile bits
+            double2 f = make_double2(1.0, 0.0);
+            if ((uint32_t)lane < p.nout) {
+                const uint32_t b = p.outpos[lane];
+                f = p.qtab[2 * b + (uint32_t)((base >> b) & 1ull)];
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                double2 g;
+                g.x = __shfl_xor_sync(0xffffffffu, f.x, off);
+                g.y = __shfl_xor_sync(0xffffffffu, f.y, off);
+                f = dcmul(f, g);
+            }
+            f.x = __shfl_sync(0xffffffffu, f.x, 0);
+            f.y = __shfl_sync(0xffffffffu, f.y, 0);
+            consumer_sync();  // everyone is done with the previous tile's products
+            for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) thigh[h] = ProdT<B>::of(dcmul(f, p.phigh[h]));
+            consumer_sync();
+        }
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
         for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 4) {
             A v[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const uint32_t j = j0 + tid + e * kTileThreads;
-                if (j < tile_amps) v[e] = buf[perm[j] ^ delta];
+                if (j < tile_amps) {
+                    if (PRODUCT) {
+                        const uint32_t src = idle ? j : ((uint32_t)perm[j] ^ delta);
+                        v[e] = ProdT<B>::mul(thigh[src >> p.l], tlow[src & lmask]);
+                    } else {
+                        v[e] = buf[perm[j] ^ delta];
+                    }
+                }
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -1191,9 +1305,13 @@ int encode_tile_map(void *state, const TilePass &t, void *map128)
 }
 
 int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d_steps,
-                int *d_err, double *d_probs, void *stream, const WaitTest *wt)
+                int *d_err, double *d_probs, void *stream, const WaitTest *wt, const double *d_prod)
 {
     TileKParams p;
+    const double2 *prod = reinterpret_cast<const double2 *>(d_prod);
+    p.qtab = prod;
+    p.plow = prod ? prod + 2 * QSIM_MAX_QUBITS : nullptr;
+    p.phigh = prod ? p.plow + (1u << t.l) : nullptr;
     p.wait_limit = (wt && wt->poll_limit) ? wt->poll_limit : kWaitLimit;
     p.stall_producer = (wt && wt->stall_producer) ? 1u : 0u;
     p.state = static_cast<char *>(state);
@@ -1237,8 +1355,13 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
         kernel<<<grid, kTileThreads + 32, smem, s>>>(p, tmap);
         return cudaGetLastError();
     };
-    if (amp_bytes == 8) e = d_probs ? run(tile_kernel<8, true>) : run(tile_kernel<8, false>);
-    else e = d_probs ? run(tile_kernel<16, true>) : run(tile_kernel<16, false>);
+    if (prod) {
+        if (amp_bytes == 8) e = d_probs ? run(tile_kernel<8, true, true>) : run(tile_kernel<8, false, true>);
+        else e = d_probs ? run(tile_kernel<16, true, true>) : run(tile_kernel<16, false, true>);
+    } else {
+        if (amp_bytes == 8) e = d_probs ? run(tile_kernel<8, true, false>) : run(tile_kernel<8, false, false>);
+        else e = d_probs ? run(tile_kernel<16, true, false>) : run(tile_kernel<16, false, false>);
+    }
     return e;
 }
 

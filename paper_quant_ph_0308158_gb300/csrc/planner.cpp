@@ -1068,6 +1068,39 @@ double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp) { return 1e3 
 
 double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp) { return 1e3 * pass_cost_s(p, M, amp); }
 
+std::vector<double> product_tables(uint32_t M, const double *qubits, const TilePass &t)
+{
+    // complex products with each real product and sum rounded separately
+    struct C {
+        double re, im;
+    };
+    auto mul = [](C a, C b) {
+        volatile double p1 = a.re * b.re, p2 = a.im * b.im, p3 = a.re * b.im, p4 = a.im * b.re;
+        return C{p1 - p2, p3 + p4};
+    };
+    auto q = [&](uint32_t b, uint32_t v) { return C{qubits[4 * b + 2 * v], qubits[4 * b + 2 * v + 1]}; };
+    std::vector<double> out(2 * (2 * QSIM_MAX_QUBITS + (1u << t.l) + (1u << t.nh)), 0.0);
+    for (uint32_t b = 0; b < M; ++b)
+        for (uint32_t v = 0; v < 2; ++v) {
+            out[2 * (2 * b + v)] = qubits[4 * b + 2 * v];
+            out[2 * (2 * b + v) + 1] = qubits[4 * b + 2 * v + 1];
+        }
+    size_t at = 2 * QSIM_MAX_QUBITS;
+    for (uint32_t u = 0; u < (1u << t.l); ++u, ++at) {
+        C c{1.0, 0.0};
+        for (uint32_t b = t.l; b-- > 0;) c = mul(c, q(b, (u >> b) & 1u));
+        out[2 * at] = c.re;
+        out[2 * at + 1] = c.im;
+    }
+    for (uint32_t h = 0; h < (1u << t.nh); ++h, ++at) {
+        C c{1.0, 0.0};
+        for (uint32_t k = t.nh; k-- > 0;) c = mul(c, q(t.high[k], (h >> k) & 1u));
+        out[2 * at] = c.re;
+        out[2 * at + 1] = c.im;
+    }
+    return out;
+}
+
 int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<SlicedStep> *out,
                     std::string *msg)
 {

@@ -501,7 +501,8 @@ static int probabilities_pass(qsim_ctx *c, double *d_probs)
 // Apply a circuit; with d_probs also write the FP64 probabilities of the
 // result, from the last pass when its kernel can (tile and gather passes),
 // else by a probabilities pass after it.
-static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_probs)
+static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_probs,
+                      const double *qubits = nullptr)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
     if (reinterpret_cast<uintptr_t>(d_probs) & 7u) return fail(QSIM_EINVAL, "d_probs misaligned");
@@ -527,7 +528,17 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     rc = make_plan(c->M, steps, L, o, &plan, &msg);
     if (rc != QSIM_OK) return fail(rc, msg);
     fill_stats(plan, c->M, c->amp, &c->stats);
+    // product input (App. 1): a first tile pass computes its sources from the
+    // qubits; any other plan starts from the state written out first
+    const bool fuse_input = qubits && !plan.passes.empty() && plan.passes[0].kind == kTile &&
+                            !plan.passes[0].tile.closed;
+    if (qubits && !fuse_input) {
+        rc = qsim_load_product_state(c, qubits);
+        if (rc != QSIM_OK) return rc;
+    }
     if (plan.passes.empty()) return d_probs ? probabilities_pass(c, d_probs) : QSIM_OK;
+    std::vector<double> prod;
+    if (fuse_input) prod = product_tables(c->M, qubits, plan.passes[0].tile);
 
     bool need_scratch = false;
     for (const Pass &p : plan.passes) need_scratch |= (p.kind == kGather);
@@ -555,13 +566,16 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     const size_t sz_sliced = plan.sliced_steps.size() * sizeof(SlicedStep);
     const size_t off_tab = align_up(off_sliced + sz_sliced, 256);
     const size_t sz_tab = plan.gather_tables.size() * sizeof(uint64_t);
-    const size_t total = off_tab + sz_tab;
+    const size_t off_prod = align_up(off_tab + sz_tab, 256);
+    const size_t sz_prod = prod.size() * sizeof(double);
+    const size_t total = off_prod + sz_prod;
     if (total > 0) {
         rc = ensure_plan_buffers(c, total);
         if (rc != QSIM_OK) return rc;
         if (sz_tile) std::memcpy(c->h_plan + off_tile, plan.tile_steps.data(), sz_tile);
         if (sz_sliced) std::memcpy(c->h_plan + off_sliced, plan.sliced_steps.data(), sz_sliced);
         if (sz_tab) std::memcpy(c->h_plan + off_tab, plan.gather_tables.data(), sz_tab);
+        if (sz_prod) std::memcpy(c->h_plan + off_prod, prod.data(), sz_prod);
         QSIM_CUDA(cudaMemcpyAsync(c->d_plan, c->h_plan, total, cudaMemcpyHostToDevice, c->stream),
                   "cudaMemcpy(plan tables)");
         QSIM_CUDA(cudaEventRecord(c->plan_ev, c->stream), "cudaEventRecord");
@@ -576,10 +590,12 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
         const Pass &p = plan.passes[pi];
         // the last pass writes the probabilities when its kernel can
         double *pp = (d_probs && pi + 1 == plan.passes.size() && p.kind != kSweep) ? d_probs : nullptr;
-        double bytes = p.alg_bytes;
+        double bytes = (pi == 0 && fuse_input) ? n * c->amp : p.alg_bytes;  // product input: writes only
         if (pp) {
             // every tile is read; touched tiles are written; plus the probabilities
-            bytes = (p.kind == kTile && !p.tile.closed ? n * c->amp + 0.5 * p.alg_bytes : p.alg_bytes) + 8.0 * n;
+            bytes = (pi == 0 && fuse_input ? n * c->amp
+                     : p.kind == kTile && !p.tile.closed ? n * c->amp + 0.5 * p.alg_bytes
+                                                         : p.alg_bytes) + 8.0 * n;
             fused = true;
         }
         const int slot = prof_begin(c, pass_variant(p), bytes);
@@ -594,7 +610,9 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
             if (jrc != QSIM_OK) return fail(jrc, jmsg);
         } else if (p.kind == kTile) {
             e = launch_tile(c->buf[c->cur], (int)c->amp, p.tile, d_tile, c->d_err, pp, c->stream,
-                            c->wait_test_armed ? &c->wait_test : nullptr);
+                            c->wait_test_armed ? &c->wait_test : nullptr,
+                            (pi == 0 && fuse_input) ? reinterpret_cast<const double *>(c->d_plan + off_prod)
+                                                    : nullptr);
             c->wait_test_armed = false;
         } else if (p.gather.jit) {
             std::string jmsg;
@@ -619,6 +637,13 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
 int qsim_apply_circuit(qsim_ctx *c, const qsim_step *steps, size_t L)
 {
     return apply_impl(c, steps, L, nullptr);
+}
+
+int qsim_apply_circuit_product(qsim_ctx *c, const double *qubits, const qsim_step *steps, size_t L,
+                               double *d_probs)
+{
+    if (!c || !qubits) return fail(QSIM_EINVAL, "NULL argument");
+    return apply_impl(c, steps, L, d_probs, qubits);
 }
 
 int qsim_apply_circuit_probabilities(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_probs)

@@ -217,8 +217,17 @@ struct WaitTest {
     uint32_t poll_limit = 0;
     bool stall_producer = false;
 };
+// d_prod non-null: product input (App. 1) -- the pass computes its source
+// amplitudes from the table block written by product_tables() instead of
+// loading them (the state's previous contents are ignored).
 int launch_tile(void *state, int amp_bytes, const TilePass &p, const TileStep *d_steps,
-                int *d_err, double *d_probs, void *stream, const WaitTest *wt = nullptr);
+                int *d_err, double *d_probs, void *stream, const WaitTest *wt = nullptr,
+                const double *d_prod = nullptr);
+// Host tables of a product-input tile pass, as FP64 complex pairs: per
+// address bit b < M its factors (q_b(0), q_b(1)) at [2b], [2b+1] (the block
+// reserves 2 * QSIM_MAX_QUBITS entries), then the products over the tile's
+// low l bits for each of their values, then over its high bits.
+std::vector<double> product_tables(uint32_t M, const double *qubits, const TilePass &t);
 int launch_gather(const void *in, void *out, int amp_bytes, uint32_t M, const GatherPass &p,
                   const uint64_t *d_tables, const SlicedStep *d_steps, int *d_err, double *d_probs,
                   void *stream);

@@ -680,3 +680,93 @@ def test_autotune_keeps_the_state_and_picks_a_working_plan(dtype, M, L, scratch)
         np.testing.assert_array_equal(sim.read_state(), want)
         with pytest.raises(QsimError):
             sim.autotune(steps, reps=0)
+
+
+# ----------------------------------------------------------------------------
+# App. 1 input fused into the first pass (qsim_apply_circuit_product)
+# ----------------------------------------------------------------------------
+
+def _assert_close_to_product(got, want, dtype):
+    """complex128: within 1e-13 of |k| (as the product-state input);
+    complex64: per part within one float ulp of the oracle's value rounded to
+    float, plus 2^-44 |k| for the float-float product of the two partial
+    products (about 2^-47 relative each way, summed over the terms of a
+    complex product, where a part can cancel)."""
+    got = got.astype(np.complex128)
+    if dtype == np.complex128:
+        assert np.all(np.abs(got - want) <= PRODUCT_RTOL * np.abs(want) + 1e-300)
+        return
+    w = want.astype(np.complex64).astype(np.complex128)
+    slack = 2.0 ** -44 * np.abs(want)
+    for g, ww in ((got.real, w.real), (got.imag, w.imag)):
+        tol = np.spacing(np.abs(ww).astype(np.float32)).astype(np.float64) + slack
+        assert np.all(np.abs(g - ww) <= tol)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("M,seed", [(12, 1), (16, 2), (20, 3), (23, 4)])
+def test_product_input_fused_into_the_first_tile_pass(cuda, dtype, M, seed):
+    torch = cuda
+    rng = np.random.default_rng(300 + M)
+    q = rng.normal(size=(M, 2)) + 1j * rng.normal(size=(M, 2))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    steps = np.concatenate([W.local_mixed_circuit(M, 150, seed, min(10, M)),
+                            W.mixed_circuit(M, 100, seed)])
+    want = oracle.apply_circuit(M, oracle.product_state(M, q), steps)
+    p = torch.full((1 << M,), -1.0, dtype=torch.float64, device="cuda")
+    with Simulator(M, dtype, scratch=False) as sim:
+        sim.set_strategy("inplace")
+        sim.set_canonicalize(False)
+        sim.set_profiling(True)
+        sim.load_state(W.random_state(M, dtype, 9))  # overwritten by the product input
+        sim.apply_product(q, steps, p.data_ptr())
+        kernels = [k for k, _, _ in sim.pass_times()]
+        got = sim.read_state()
+    assert kernels[0] == "tile_kernel" and "probs_kernel" not in kernels
+    _assert_close_to_product(got, want, dtype)
+    # the probabilities are those of the amplitudes stored
+    assert_probs_close(p.cpu().numpy(), oracle.probabilities(got))
+
+
+def test_product_input_falls_back_when_the_plan_starts_with_a_gather():
+    M = 14
+    rng = np.random.default_rng(14)
+    q = rng.normal(size=(M, 2)) + 1j * rng.normal(size=(M, 2))
+    steps = W.mixed_circuit(M, 400, 14)
+    want = oracle.apply_circuit(M, oracle.product_state(M, q), steps)
+    with Simulator(M, np.complex128) as sim:
+        sim.set_strategy("gather")
+        sim.set_profiling(True)
+        sim.apply_product(q, steps)
+        kernels = [k for k, _, _ in sim.pass_times()]
+        got = sim.read_state()
+    assert kernels[0] != "tile_kernel"
+    _assert_close_to_product(got, want, np.complex128)
+
+
+def test_sec4_parity_m32_fused_product_input(cuda):
+    """The Sec. 4 example at M = 32 with its input generated inside the one
+    tile pass: every amplitude (-1)^popcount(i) / 2^16 exactly (checked on the
+    device), every probability exactly 2^-32."""
+    torch = cuda
+    M = 32
+    cfg = W.config_parity(M)
+    probs = torch.empty(1 << M, dtype=torch.float64, device="cuda")
+    with Simulator(M, np.complex64, scratch=False) as sim:
+        sim.set_strategy("inplace")
+        sim.set_profiling(True)
+        sim.apply_product(cfg["qubits"], cfg["steps"], probs.data_ptr())
+        sim.synchronize()
+        assert [k for k, _, _ in sim.pass_times()] == ["tile_kernel"]
+        st = sim.state_tensor().view(torch.float32).view(-1, 2)
+        assert bool((st[:, 1] == 0).all())
+        re = st[:, 0]
+        assert bool((re.abs() == 2.0 ** -16).all())
+        rng = np.random.default_rng(3232)
+        rows = rng.integers(0, 1 << M, size=1 << 16, dtype=np.uint64)
+        got = re[torch.from_numpy(rows.astype(np.int64)).cuda()].cpu().numpy()
+        par = np.zeros_like(rows)
+        for b in range(M):
+            par ^= (rows >> np.uint64(b)) & np.uint64(1)
+        np.testing.assert_array_equal(got, np.where(par.astype(bool), -1.0, 1.0).astype(np.float32) * 2.0 ** -16)
+        assert bool((probs == 2.0 ** -32).all())
