@@ -327,7 +327,6 @@ __device__ __forceinline__ void tr32(u32 (&a)[32])
 #define BOX_BYTES @BOX@
 #define TABN ((NT * 33 + 7) / 8 * 8)  /* exchange-table entries, rounded to 16 bytes */
 #define STAGES @STAGES@
-#define REGSTAGE @REGSTAGE@
 __device__ __forceinline__ u64 tile_base(u64 t) { u64 b = 0; @TILEBASE@ return b; }
 __device__ __forceinline__ u64 deposit_high(u32 r) { u64 d = 0; @DEPHIGH@ return d; }
 __device__ __forceinline__ u64 deposit_rest(u32 r) { u64 d = 0; @DEPREST@ return d; }
@@ -399,23 +398,6 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
       return;
     }
     const Amp *buf = bufs + ((size_t)1 << K) * s;
-#if REGSTAGE
-    // one stage: take all 32 values into registers and release the stage
-    // before the stores and probabilities, so the next tile loads meanwhile
-    Amp v[32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] = buf[tab[e * 33 + lane]];
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      const u32 j = ((u32)warp * 32u + (u32)e) * 32u + (u32)lane;
-      const u64 g = base + depo[j >> L] + (j & ((1u << L) - 1u));
-      reinterpret_cast<Amp *>(p.state)[g] = v[e];
-      if (p.probs) p.probs[g] = AMP_PROB(v[e]);
-    }
-    continue;
-#endif
 #pragma unroll 1
     for (int e0 = 0; e0 < 32; e0 += 8) {
       Amp v[8];
@@ -466,10 +448,6 @@ uint32_t closed_stages(int amp, const TilePass &t)
     return st < 1 ? 1 : (uint32_t)st;
 }
 
-// Values held in registers between the shared-memory reads and the stores:
-// with a single complex64 stage (32 values are 64 registers).
-bool closed_regstage(int amp, const TilePass &t) { return amp == 8 && closed_stages(amp, t) == 1; }
-
 std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
 {
     std::string src = kClosedTemplate;
@@ -519,7 +497,6 @@ std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, 
     replace_all(src, "@B@", std::to_string(amp));
     replace_all(src, "@BOX@", std::to_string(t.box_bytes));
     replace_all(src, "@STAGES@", std::to_string(closed_stages(amp, t)));
-    replace_all(src, "@REGSTAGE@", closed_regstage(amp, t) ? "1" : "0");
     replace_all(src, "@TILEBASE@", tb.str());
     replace_all(src, "@DEPHIGH@", dh.str());
     replace_all(src, "@DEPREST@", dr.str());
@@ -533,8 +510,7 @@ std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, 
 
 std::vector<uint64_t> closed_key(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
 {
-    std::vector<uint64_t> k = {0xC105EDull, M, (uint64_t)amp, t.k, t.l, t.nh, t.nrest, t.box_bytes, t.nout,
-                               closed_regstage(amp, t) ? 1ull : 0ull};
+    std::vector<uint64_t> k = {0xC105EDull, M, (uint64_t)amp, t.k, t.l, t.nh, t.nrest, t.box_bytes, t.nout};
     for (uint32_t q = 0; q < t.nh; ++q) k.push_back(t.high[q]);
     for (uint32_t q = 0; q < t.nrest; ++q) k.push_back(t.rest_pos[q]);
     for (uint32_t q = 0; q < 6; ++q) k.push_back(t.tma_start[q]);

@@ -319,9 +319,9 @@ def test_adder_m32_workload_sampled():
 def test_adder_m32_benchmarked_closed_pass_sampled():
     """M=32 complex64 adder in place as benchmarked: compiled kernels on, so
     the whole circuit is one closed tile pass (its net map changes only
-    b_4..b_14 and the carry-out) that also writes the probabilities."""
+    b_4..b_14 and the carry-out), then the probabilities' own pass."""
     st, kernels = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 20, jit=True, probs=True)
-    assert st["passes"] == 1 and kernels == ["qsim_jit_closed"]
+    assert st["passes"] == 1 and kernels == ["qsim_jit_closed", "probs_kernel"]
 
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
