@@ -444,6 +444,8 @@ typedef struct qsim_server_stats {
     double issue_ms, issue_ms_max; /* host time spent issuing the copies (total,
                                       longest): a copy from host memory that is
                                       not pinned runs while it is issued */
+    uint64_t evicted;           /* running requests swapped out to host memory  */
+    uint64_t swapped_in;        /* of them brought back to the device           */
 } qsim_server_stats;
 
 /* Reserve hbm_budget_bytes of device memory (one cudaMalloc) and a pinned
@@ -494,6 +496,17 @@ int qsim_server_set_copy_streams(qsim_server *s, int n);
  * copy per state); bytes must be 0 or at least 1 MiB and a multiple of 256
  * (QSIM_EINVAL otherwise).  Applies to requests admitted afterwards. */
 int qsim_server_set_upload_chunk(qsim_server *s, size_t bytes);
+
+/* Eviction (off by default, evict_after_ms < 0): once the head of the queue
+ * has waited evict_after_ms without fitting the budget, running requests --
+ * the most recently admitted first, between their passes -- are copied out
+ * to blocks of the host result arena and their device memory returns to the
+ * budget until the head fits (Sec. 1 and Sec. 5 trade memory for
+ * processing; here whole states move to host memory and back).  A
+ * swapped-out request returns, ahead of everything but the head, as soon as
+ * it fits, and runs on from its next pass with the same result bits.  A
+ * request is evicted only if its state fits the host arena. */
+int qsim_server_set_eviction(qsim_server *s, double evict_after_ms);
 
 /* Pause (paused != 0) or resume admission.  While paused, submitted requests
  * wait and admitted ones run to completion; e.g. to submit a group of

@@ -58,7 +58,7 @@ EXPORTS = (
     "qsim_server_submit", "qsim_server_poll", "qsim_server_release", "qsim_server_wait_all",
     "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain", "qsim_server_set_backfill",
     "qsim_server_set_paused", "qsim_server_set_tracing", "qsim_server_get_trace",
-    "qsim_server_set_copy_streams", "qsim_server_set_upload_chunk",
+    "qsim_server_set_copy_streams", "qsim_server_set_upload_chunk", "qsim_server_set_eviction",
 )
 
 
@@ -108,7 +108,8 @@ class ServerStats(ctypes.Structure):
                 ("backfilled", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
                 ("d2h_bytes", ctypes.c_uint64), ("h2d_busy_ms", ctypes.c_double),
                 ("d2h_busy_ms", ctypes.c_double), ("compute_busy_ms", ctypes.c_double),
-                ("issue_ms", ctypes.c_double), ("issue_ms_max", ctypes.c_double)]
+                ("issue_ms", ctypes.c_double), ("issue_ms_max", ctypes.c_double),
+                ("evicted", ctypes.c_uint64), ("swapped_in", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -207,6 +208,7 @@ def load() -> ctypes.CDLL:
             "qsim_server_set_paused": ([p, i], i),
             "qsim_server_set_copy_streams": ([p, i], i),
             "qsim_server_set_upload_chunk": ([p, sz], i),
+            "qsim_server_set_eviction": ([p, ctypes.c_double], i),
             "qsim_server_set_tracing": ([p, i], i),
             "qsim_server_get_trace": ([p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_server_destroy": ([p], None),
@@ -618,6 +620,11 @@ class Server:
     def set_copy_streams(self, n: int):
         """Copies in and out on two overlapping streams (2) or one stream (1)."""
         _check(self._lib.qsim_server_set_copy_streams(self._s, int(n)))
+
+    def set_eviction(self, evict_after_ms: float):
+        """Swap running requests out to host memory for a head that waited
+        this long (negative: off)."""
+        _check(self._lib.qsim_server_set_eviction(self._s, float(evict_after_ms)))
 
     def set_upload_chunk(self, nbytes: int):
         _check(self._lib.qsim_server_set_upload_chunk(self._s, nbytes))

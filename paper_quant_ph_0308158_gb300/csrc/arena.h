@@ -53,6 +53,7 @@ class Arena {
         free_[off] = bytes;
     }
     size_t used() const { return used_; }
+    size_t capacity() const { return size_; }
     size_t peak() const { return peak_; }
     size_t size() const { return size_; }
     // the free blocks and the allocated ones: offset -> length, ascending

@@ -71,7 +71,13 @@ struct Request {
     bool probs_fused = false;  // the last pass writes the probabilities (and no state)
     int probs_buf = -1;        // buffer holding the probabilities
     double compute_start_ms = -1, compute_end_ms = -1;  // rounds that ran its passes (trace)
-    enum State { kWaiting, kUploading, kRunning, kComputing, kFinishing, kDone } state = kWaiting;
+    enum State { kWaiting, kUploading, kRunning, kComputing, kFinishing, kDone, kDraining, kSwappingOut,
+                 kSwappedOut }
+        state = kWaiting;
+    int last_slot = -1;        // round slot of the last round that ran one of its passes
+    size_t swap_off = 0;       // host block holding its state while swapped out
+    bool swap_held = false;
+    cudaEvent_t swapped = nullptr;  // the state's copy out (eviction) is done
     cudaEvent_t uploaded = nullptr, computed = nullptr, finished = nullptr;
     cudaEvent_t up0 = nullptr, down0 = nullptr;  // timing: starts of the two copies
     Clock::time_point t_submit, t_admit, t_done;
@@ -108,6 +114,9 @@ struct qsim_server {
     size_t pending_upload_bytes = 0;  // admitted states not yet on the device
     int copy_streams = 2;             // 2: copies in and out overlap; 1: one copy stream
     size_t upload_chunk = 0;          // state uploads in copies of at most this many bytes (0: one)
+    double evict_after_ms = -1.0;     // evict running requests for a head that waited this long
+    uint64_t evicting_for = 0;        // head request id that evictions are making room for
+    std::deque<std::shared_ptr<Request>> swapped;  // evicted requests, in eviction order
     cudaEvent_t t0_event = nullptr;   // device-time origin of the trace
     Clock::time_point t0;             // host-time origin of the trace
     bool tracing = false;
@@ -253,19 +262,121 @@ Admit try_admit(qsim_server *s, const std::shared_ptr<Request> &r)
     return kAdmitted;
 }
 
+// A swapped-out request comes back: its blocks are allocated again, its state
+// is copied into the buffer that held it (so the plan's ping-pong and block
+// sizes stay as at admission) and its tables are copied again; it then runs
+// on from its next pass.  Called with the lock held.
+bool try_swap_in(qsim_server *s, const std::shared_ptr<Request> &r)
+{
+    const size_t n = 1ull << r->M;
+    if (s->pending_upload_bytes >= kMaxPendingUpload) return false;
+    size_t sl_off = 0;
+    const size_t tb = tables_bytes(r->plan, &sl_off);
+    if (!s->dev.alloc(r->bytes[0], &r->off[0])) return false;
+    if (!s->dev.alloc(r->bytes[1], &r->off[1])) {
+        s->dev.release(r->off[0]);
+        return false;
+    }
+    r->held[0] = r->held[1] = true;
+    r->buf[0] = s->d_arena + r->off[0];
+    r->buf[1] = s->d_arena + r->off[1];
+    r->d_tab = r->buf[0] + align256(n * s->amp);
+    const char *h_tab = s->h_arena + r->host_off + align256(n * 8);
+    cudaError_t e = cudaEventRecord(r->up0, s->h2d);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->buf[r->cur], s->h_arena + r->swap_off, n * s->amp, cudaMemcpyHostToDevice, s->h2d);
+    if (e == cudaSuccess && tb) e = cudaMemcpyAsync(r->d_tab, h_tab, tb, cudaMemcpyHostToDevice, s->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(r->uploaded, s->h2d);
+    if (e != cudaSuccess) {
+        if (!s->worker_error.size()) s->worker_error = std::string("swap-in copy: ") + cudaGetErrorString(e);
+        return false;
+    }
+    s->st.h2d_bytes += n * s->amp;
+    s->pending_upload_bytes += n * s->amp;
+    r->state = Request::kUploading;
+    s->active.push_back(r);
+    ++s->st.swapped_in;
+    return true;
+}
+
+// Copy an evicted request's state out to a host block once its last round
+// has finished; its device blocks return to the budget when the copy is done.
+// Returns false if it must wait (round still running, or no host block yet).
+bool start_swap_out(qsim_server *s, const std::shared_ptr<Request> &r)
+{
+    if (r->last_slot >= 0 && cudaEventQuery(s->slots[r->last_slot].done) != cudaSuccess) return false;
+    const size_t n = 1ull << r->M;
+    size_t off = 0;
+    if (!s->host.alloc(n * s->amp, &off)) return false;
+    cudaStream_t st = s->copy_streams == 1 ? s->h2d : s->d2h;
+    cudaError_t e = cudaMemcpyAsync(s->h_arena + off, r->buf[r->cur], n * s->amp, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(r->swapped, st);
+    if (e != cudaSuccess) {
+        s->host.release(off);
+        if (s->worker_error.empty()) s->worker_error = std::string("eviction copy: ") + cudaGetErrorString(e);
+        return false;
+    }
+    r->swap_off = off;
+    r->swap_held = true;
+    r->state = Request::kSwappingOut;
+    s->st.d2h_bytes += n * s->amp;
+    return true;
+}
+
+// Make room for the head of the queue, which has waited evict_after_ms: the
+// running requests admitted most recently leave the rounds (they drain), and
+// once their last round has finished their states are copied out to host
+// blocks (start_swap_out) -- the paper's trade of memory for processing
+// (Sec. 1, Sec. 5) applied to whole states.  Called with the lock held.
+void evict_for(qsim_server *s, const std::shared_ptr<Request> &head)
+{
+    for (const auto &r : s->active)
+        if (r->state == Request::kDraining || r->state == Request::kSwappingOut) return;  // under way
+    size_t hb[2];
+    block_sizes(head->plan, head->M, s->amp, hb);
+    const size_t need = hb[0] + hb[1];
+    size_t freed = s->dev.capacity() - s->dev.used();
+    const size_t host_free = s->host.capacity() - s->host.used();
+    size_t host_need = 0;
+    for (auto it = s->active.rbegin(); it != s->active.rend() && freed < need; ++it) {
+        const auto &r = *it;
+        if (r->state != Request::kRunning || r->next_pass >= r->plan.passes.size()) continue;
+        const size_t n = 1ull << r->M;
+        if (host_need + n * s->amp > host_free) continue;
+        host_need += n * s->amp;
+        r->state = Request::kDraining;
+        ++s->st.evicted;
+        freed += r->bytes[0] + r->bytes[1];
+        s->evicting_for = head->id;
+    }
+}
+
 // Admission: FIFO, except that while the head of the queue does not fit and
 // has waited less than max_head_wait_ms, later requests that fit are admitted
 // ahead of it (backfill); after that nothing passes the head, so the budget
-// drains until it fits.  Called with the lock held.
+// drains until it fits -- or, with eviction on, running requests are swapped
+// out to host memory for it once it has waited evict_after_ms.  Swapped-out
+// requests come back as soon as they fit, ahead of everything but the head.
+// Called with the lock held.
 void admit(qsim_server *s)
 {
     constexpr size_t kWindow = 256;  // requests looked at behind the head
     if (s->paused) return;
-    while (!s->waiting.empty() && try_admit(s, s->waiting.front()) != kNotAdmitted) s->waiting.pop_front();
-    if (s->waiting.empty() || s->max_head_wait_ms < 0) return;
+    while (!s->waiting.empty() && try_admit(s, s->waiting.front()) != kNotAdmitted) {
+        if (s->waiting.front()->id == s->evicting_for) s->evicting_for = 0;
+        s->waiting.pop_front();
+    }
+    if (s->waiting.empty()) s->evicting_for = 0;
+    if (!s->evicting_for)  // the memory freed for a head is the head's first
+        for (auto it = s->swapped.begin(); it != s->swapped.end();) {
+            if (try_swap_in(s, *it)) it = s->swapped.erase(it);
+            else ++it;
+        }
+    if (s->waiting.empty()) return;
     const double head_wait =
         std::chrono::duration<double, std::milli>(Clock::now() - s->waiting.front()->t_submit).count();
-    if (head_wait >= s->max_head_wait_ms) return;
+    if (s->evict_after_ms >= 0 && head_wait >= s->evict_after_ms) evict_for(s, s->waiting.front());
+    if (s->max_head_wait_ms < 0 || head_wait >= s->max_head_wait_ms || s->evicting_for) return;
     size_t looked = 0;
     for (auto it = std::next(s->waiting.begin()); it != s->waiting.end() && looked < kWindow; ++looked) {
         const Admit a = try_admit(s, *it);
@@ -406,8 +517,10 @@ bool run_round(qsim_server *s, std::vector<std::shared_ptr<Request>> &ready)
     ++s->st.rounds;
     ++s->st.launches;
     // requests whose last pass was just queued: probabilities, then copy out
-    for (auto &r : ready)
+    for (auto &r : ready) {
+        r->last_slot = (int)(&sl - s->slots);
         if (r->next_pass == r->plan.passes.size()) finish_request(s, r);
+    }
     return true;
 }
 
@@ -500,18 +613,37 @@ void worker_loop(qsim_server *s)
                 }
             }
             retire_rounds(s);  // after the completions: their rounds are done
+            // evicted states copied out: their device blocks return to the budget
+            for (auto it = s->active.begin(); it != s->active.end();) {
+                auto &r = *it;
+                if (r->state == Request::kDraining) start_swap_out(s, r);
+                if (r->state == Request::kSwappingOut && cudaEventQuery(r->swapped) == cudaSuccess) {
+                    for (int b = 0; b < 2; ++b)
+                        if (r->held[b]) s->dev.release(r->off[b]);
+                    r->held[0] = r->held[1] = false;
+                    r->state = Request::kSwappedOut;
+                    s->swapped.push_back(r);
+                    it = s->active.erase(it);
+                } else {
+                    ++it;
+                }
+            }
             admit(s);
             for (auto &r : s->active) {
                 if (r->state == Request::kUploading && cudaEventQuery(r->uploaded) == cudaSuccess) {
                     r->state = Request::kRunning;
                     s->pending_upload_bytes -= (1ull << r->M) * s->amp;
+                    if (r->swap_held) {  // back from host memory
+                        s->host.release(r->swap_off);
+                        r->swap_held = false;
+                    }
                     if (r->plan.passes.empty()) finish_request(s, r);  // nothing to apply
                 }
                 if (r->state == Request::kRunning && r->next_pass < r->plan.passes.size())
                     ready.push_back(r);
             }
             if (!ready.empty()) launched = run_round(s, ready);
-            idle = ready.empty() && s->waiting.empty() && s->active.empty();
+            idle = ready.empty() && s->waiting.empty() && s->active.empty() && s->swapped.empty();
             s->st.active = s->active.size();
             s->st.waiting = s->waiting.size();
             s->st.in_use_bytes = s->dev.used();
@@ -596,6 +728,7 @@ int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const 
     cudaEventCreate(&r->finished);
     cudaEventCreate(&r->up0);
     cudaEventCreate(&r->down0);
+    cudaEventCreateWithFlags(&r->swapped, cudaEventDisableTiming);
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     s->waiting.push_back(r);
@@ -654,6 +787,7 @@ int qsim_server_release(qsim_server *s, uint64_t id)
     cudaEventDestroy(it->second->finished);
     cudaEventDestroy(it->second->up0);
     cudaEventDestroy(it->second->down0);
+    cudaEventDestroy(it->second->swapped);
     s->all.erase(it);
     s->cv.notify_all();
     return QSIM_OK;
@@ -664,10 +798,10 @@ int qsim_server_wait_all(qsim_server *s, double timeout_s)
     if (!s) return sfail(QSIM_EINVAL, "NULL argument");
     std::unique_lock<std::mutex> lk(s->mu);
     const auto until = Clock::now() + std::chrono::duration<double>(timeout_s);
-    while (!(s->waiting.empty() && s->active.empty())) {
+    while (!(s->waiting.empty() && s->active.empty() && s->swapped.empty())) {
         if (!s->worker_error.empty()) return sfail(QSIM_ECUDA, s->worker_error);
         if (s->cv.wait_until(lk, until) == std::cv_status::timeout &&
-            !(s->waiting.empty() && s->active.empty()))
+            !(s->waiting.empty() && s->active.empty() && s->swapped.empty()))
             return sfail(QSIM_ETIMEOUT, "requests still pending");
     }
     return QSIM_OK;
@@ -714,6 +848,15 @@ int qsim_server_get_trace(qsim_server *s, qsim_server_trace_record *out, size_t 
     if (n) std::memcpy(out, s->trace.data(), n * sizeof(qsim_server_trace_record));
     s->trace.erase(s->trace.begin(), s->trace.begin() + (std::ptrdiff_t)n);
     *n_out = n;
+    return QSIM_OK;
+}
+
+int qsim_server_set_eviction(qsim_server *s, double evict_after_ms)
+{
+    if (!s) return sfail(QSIM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->evict_after_ms = evict_after_ms;
+    s->cv.notify_all();
     return QSIM_OK;
 }
 

@@ -209,3 +209,47 @@ def test_served_large_requests_alone_and_in_the_mix():
             assert done
             np.testing.assert_array_equal(p, mixed[M])
             srv.release(r)
+
+
+def test_eviction_makes_room_for_the_head_and_results_stay_exact():
+    """Long-running requests fill the HBM budget; a larger request arrives.
+    With eviction on, running requests are swapped out to host memory between
+    their passes, the newcomer is admitted, and the evicted requests come back
+    and finish: every result equals the oracle's and the same requests served
+    without eviction, bit for bit."""
+    Ms, Mb = 20, 22
+    smalls = [(Ms, W.random_state(Ms, np.complex128, 40 + i), W.mixed_circuit(Ms, 400000, 40 + i))
+              for i in range(6)]
+    big = (Mb, W.random_state(Mb, np.complex128, 77), W.cnot_circuit(Mb, 800, 77))
+    reqs = smalls + [big]
+
+    def serve(evict):
+        out = {}
+        with Server(256 << 20, 512 << 20, np.complex128) as srv:
+            srv.set_backfill(-1)
+            if evict:
+                srv.set_eviction(0.0)
+            ids = [srv.submit(M, k1, st) for (M, k1, st) in smalls]
+            deadline = time.time() + 60
+            while srv.stats()["active"] < len(smalls) and time.time() < deadline:
+                time.sleep(0.001)
+            ids.append(srv.submit(*big))
+            srv.wait_all(600)
+            st = srv.stats()
+            assert st["completed"] == len(reqs)
+            for rid, (M, k1, steps) in zip(ids, reqs):
+                done, _, p = srv.poll(rid)
+                assert done
+                out[rid] = p.copy()
+                srv.release(rid)
+            assert srv.stats()["host_in_use_bytes"] == 0 and srv.stats()["in_use_bytes"] == 0
+        return [out[i] for i in ids], st
+
+    with_ev, st = serve(True)
+    assert st["evicted"] >= 1 and st["swapped_in"] == st["evicted"]
+    without, st0 = serve(False)
+    assert st0["evicted"] == 0
+    for a, b in zip(with_ev, without):
+        np.testing.assert_array_equal(a, b)
+    for p, (M, k1, steps) in zip(with_ev, reqs):
+        assert_probs_close(p, _expected(M, k1, steps))
