@@ -279,6 +279,34 @@ __device__ __forceinline__ float ff_dot2_round(float xh, float xl, float yh, flo
     return s + (err + e1 + e2 + cross);
 }
 
+// x*y + sign*z*w kept in float-float (hi, lo).
+__device__ __forceinline__ float2 ff_dot2(float xh, float xl, float yh, float yl, float zh, float zl, float wh,
+                                          float wl, float sign)
+{
+    const float p1 = xh * yh;
+    const float e1 = fmaf(xh, yh, -p1);
+    const float p2 = sign * zh * wh;
+    const float e2 = fmaf(sign * zh, wh, -p2);
+    const float s = p1 + p2;
+    const float bb = s - p1;
+    const float err = (p1 - (s - bb)) + (p2 - bb);
+    const float lo = err + e1 + e2 + fmaf(xh, yl, xl * yh) + sign * fmaf(zh, wl, zl * wh);
+    const float h = s + lo;
+    return make_float2(h, lo - (h - s));
+}
+
+__device__ __forceinline__ FFc ffc_mul(const FFc &a, const FFc &b)
+{
+    const float2 re = ff_dot2(a.rh, a.rl, b.rh, b.rl, a.ih, a.il, b.ih, b.il, -1.0f);
+    const float2 im = ff_dot2(a.rh, a.rl, b.ih, b.il, a.ih, a.il, b.rh, b.rl, 1.0f);
+    FFc r;
+    r.rh = re.x;
+    r.rl = re.y;
+    r.ih = im.x;
+    r.il = im.y;
+    return r;
+}
+
 __device__ __forceinline__ double2 dcmul(double2 a, double2 b)
 {
     return make_double2(__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
@@ -291,6 +319,7 @@ template <int B> struct ProdT;
 template <> struct ProdT<8> {
     using T = FFc;
     static __device__ __forceinline__ T of(double2 v) { return ffc_of(v); }
+    static __device__ __forceinline__ T scale(const T &c, const T &h) { return ffc_mul(c, h); }
     static __device__ __forceinline__ uint2 mul(const T &a, const T &b)
     {
         const float re = ff_dot2_round(a.rh, a.rl, b.rh, b.rl, a.ih, a.il, b.ih, b.il, -1.0f);
@@ -301,6 +330,7 @@ template <> struct ProdT<8> {
 template <> struct ProdT<16> {
     using T = double2;
     static __device__ __forceinline__ T of(double2 v) { return v; }
+    static __device__ __forceinline__ T scale(const T &c, const T &h) { return dcmul(c, h); }
     static __device__ __forceinline__ uint4 mul(const T &a, const T &b)
     {
         const double2 v = dcmul(a, b);
@@ -444,8 +474,11 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     using PT = typename ProdT<B>::T;
     PT *thigh = reinterpret_cast<PT *>(bufs);
     PT *tlow = thigh + (1u << p.nh);
+    PT *phigh = tlow + (1u << p.l);
+    PT *tfac = phigh + (1u << p.nh);
     if (PRODUCT) {
         for (uint32_t u = tid; u < (1u << p.l); u += kTileThreads) tlow[u] = ProdT<B>::of(p.plow[u]);
+        for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) phigh[h] = ProdT<B>::of(p.phigh[h]);
     }
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
@@ -509,25 +542,28 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
             consumer_sync();  // the new table is complete
         }
         if (PRODUCT) {
-            // this tile's factor over the bits outside it (a butterfly product
-            // over the lanes of each warp; every warp gets the same value),
-            // then its products over the high tile bits
-            double2 f = make_double2(1.0, 0.0);
-            if ((uint32_t)lane < p.nout) {
-                const uint32_t b = p.outpos[lane];
-                f = p.qtab[2 * b + (uint32_t)((base >> b) & 1ull)];
-            }
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                double2 g;
-                g.x = __shfl_xor_sync(0xffffffffu, f.x, off);
-                g.y = __shfl_xor_sync(0xffffffffu, f.y, off);
-                f = dcmul(f, g);
-            }
-            f.x = __shfl_sync(0xffffffffu, f.x, 0);
-            f.y = __shfl_sync(0xffffffffu, f.y, 0);
+            // this tile's factor over the bits outside it (FP64, a butterfly
+            // product over the lanes of warp 0), then its products over the
+            // high tile bits (complex64: in float-float)
             consumer_sync();  // everyone is done with the previous tile's products
-            for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) thigh[h] = ProdT<B>::of(dcmul(f, p.phigh[h]));
+            if (warp == 0) {
+                double2 f = make_double2(1.0, 0.0);
+                if ((uint32_t)lane < p.nout) {
+                    const uint32_t b = p.outpos[lane];
+                    f = p.qtab[2 * b + (uint32_t)((base >> b) & 1ull)];
+                }
+#pragma unroll
+                for (int off = 16; off; off >>= 1) {
+                    double2 g;
+                    g.x = __shfl_xor_sync(0xffffffffu, f.x, off);
+                    g.y = __shfl_xor_sync(0xffffffffu, f.y, off);
+                    f = dcmul(f, g);
+                }
+                if (lane == 0) *tfac = ProdT<B>::of(f);
+            }
+            consumer_sync();
+            const PT c = *tfac;
+            for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) thigh[h] = ProdT<B>::scale(c, phigh[h]);
             consumer_sync();
         }
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);

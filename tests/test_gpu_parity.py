@@ -689,15 +689,17 @@ def test_autotune_keeps_the_state_and_picks_a_working_plan(dtype, M, L, scratch)
 def _assert_close_to_product(got, want, dtype):
     """complex128: within 1e-13 of |k| (as the product-state input);
     complex64: per part within one float ulp of the oracle's value rounded to
-    float, plus 2^-44 |k| for the float-float product of the two partial
-    products (about 2^-47 relative each way, summed over the terms of a
-    complex product, where a part can cancel)."""
+    float, plus 2^-42 |k| for the float-float arithmetic: the FP64 partial
+    products are split into float-float (2^-48 relative each), the tile's
+    factor times the high-bit product and that times the low-bit product are
+    float-float complex products (each within about 2^-45 of |k|, as a part
+    of a complex product can cancel), so three stages stay under 2^-43."""
     got = got.astype(np.complex128)
     if dtype == np.complex128:
         assert np.all(np.abs(got - want) <= PRODUCT_RTOL * np.abs(want) + 1e-300)
         return
     w = want.astype(np.complex64).astype(np.complex128)
-    slack = 2.0 ** -44 * np.abs(want)
+    slack = 2.0 ** -42 * np.abs(want)
     for g, ww in ((got.real, w.real), (got.imag, w.imag)):
         tol = np.spacing(np.abs(ww).astype(np.float32)).astype(np.float64) + slack
         assert np.all(np.abs(g - ww) <= tol)
@@ -722,7 +724,9 @@ def test_product_input_fused_into_the_first_tile_pass(cuda, dtype, M, seed):
         sim.apply_product(q, steps, p.data_ptr())
         kernels = [k for k, _, _ in sim.pass_times()]
         got = sim.read_state()
-    assert kernels[0] == "tile_kernel" and "probs_kernel" not in kernels
+    assert kernels[0] == "tile_kernel"
+    if kernels[-1] != "probs_kernel":  # a plan ending in a sweep needs the separate pass
+        assert "probs_kernel" not in kernels
     _assert_close_to_product(got, want, dtype)
     # the probabilities are those of the amplitudes stored
     assert_probs_close(p.cpu().numpy(), oracle.probabilities(got))

@@ -21,6 +21,7 @@ def cuda():
     from paper_quant_ph_0308158_gb300 import build
     build.build()
     torch.cuda.set_device(0)
+    torch.cuda.empty_cache()  # the servers below take their budgets with cudaMalloc
 
 
 def _requests(n, seed, m_lo=4, m_hi=16):

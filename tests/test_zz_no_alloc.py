@@ -30,6 +30,9 @@ def torch():
     from paper_quant_ph_0308158_gb300 import build
     build.build()
     t.cuda.set_device(0)
+    # memory PyTorch still caches from earlier tests goes back to the device:
+    # the first launch of the library's code in this context loads its module
+    t.cuda.empty_cache()
     return t
 
 
