@@ -342,7 +342,8 @@ class Resident:
     host input and what the timed region measured."""
 
 
-def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, sample_clocks=True):
+def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, sample_clocks=True,
+                     for_e2e=True):
     """Time steps_k steps of one workload on a resident state (after warmup
     untimed steps), CUDA events on the context's stream, max over ranks.
 
@@ -361,7 +362,7 @@ def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, s
     # end-to-end leg copies that state in from the host all the same
     qubits = cfg.get("qubits")
     h_in = None
-    if qubits is None or not args.no_e2e:
+    if qubits is None or (for_e2e and not args.no_e2e):
         h_in = torch.empty(n, dtype=tdt, pin_memory=True).numpy()
         if qubits is None:
             W.random_state(M, dtype, cfg["state_seed"], out=h_in)
@@ -565,7 +566,7 @@ def run_ours(args, rank, ws, local):
             continue
         c2 = workload(wl)
         r2 = measure_resident(args, c2, strategy_for(wl), args.jit, local, ws, args.steps,
-                              args.warmup, sample_clocks=False)
+                              args.warmup, sample_clocks=False, for_e2e=False)
         r2.sim.close()
         pure = None
         if wl == "hybrid_m28":  # the same circuit forced into one strategy
@@ -1109,7 +1110,7 @@ def main():
     ap.add_argument("--coset-stage-kib", type=int, default=0, help="coset pipeline stage (0: 32 KiB)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison of the default run")
-    ap.add_argument("--also", default="mixed_m28,cnot_m28,hybrid_m28",
+    ap.add_argument("--also", default="mixed_m28,cnot_m28,hybrid_m28,parity_m32",
                     help="comma-separated single-circuit workloads also timed on the same line "
                          "(device-resident, no e2e); empty: none")
     ap.add_argument("--batch-compare", type=int, default=4096,
