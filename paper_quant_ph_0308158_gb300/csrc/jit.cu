@@ -420,203 +420,7 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
 }
 )QSIMSRC";
 
-// Closed tile pass split over a cluster of two CTAs: each holds one half of
-// every tile (the tile's top local bit is its rank) in a two-stage pipeline,
-// and reads the sources in the other half from its partner's shared memory.
-// A relay warp tells the partner when this CTA's half of a stage has landed;
-// consumers release a stage in both CTAs.  Every wait on an mbarrier is
-// bounded; on a failed wait a thread records the error and leaves its loop,
-// so both CTAs still meet at the closing cluster barrier.
-const char *kClosedClusterTemplate = R"QSIMSRC(
-typedef unsigned int u32;
-typedef unsigned long long u64;
-typedef unsigned short u16;
-struct __align__(64) TMap { u64 v[16]; };
-struct Params { char *state; double *probs; int *err; u64 n_tiles; u32 wait_limit; u32 pad; };
-#define QSIM_Q __device__ __forceinline__
-#define QSIM_QN __device__ __noinline__
-@PROBMATH@
-@AMPDEF@
-__device__ __forceinline__ u32 sa(const void *p) { return (u32)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ u32 peer_addr(u32 a, u32 rank)
-{ u32 r; asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank)); return r; }
-__device__ __forceinline__ void mbar_init(u64 *b, u32 c)
-{ asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sa(b)), "r"(c) : "memory"); }
-__device__ __forceinline__ void mbar_expect(u64 *b, u32 bytes)
-{ asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" :: "r"(sa(b)), "r"(bytes) : "memory"); }
-__device__ __forceinline__ void mbar_arrive(u64 *b)
-{ asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(sa(b)) : "memory"); }
-__device__ __forceinline__ void mbar_arrive_remote(u32 cluster_addr)
-{ asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(cluster_addr) : "memory"); }
-__device__ __forceinline__ bool mbar_wait(u64 *b, u32 parity, u32 limit)
-{
-  for (u32 w = 0; w < limit; ++w) {
-    u32 ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(sa(b)), "r"(parity) : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void cluster_sync()
-{
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ u32 cluster_rank()
-{ u32 r; asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r)); return r; }
-__device__ __forceinline__ void tma5(void *dst, const TMap *m, int c0, int c1, int c2, int c3, int c4, u64 *bar)
-{
-  asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-               " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-               :: "r"(sa(dst)), "l"((u64)m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(sa(bar)) : "memory");
-}
-__device__ __forceinline__ Amp lds_amp(u32 addr) { Amp v; @LDS_LOCAL@ return v; }
-__device__ __forceinline__ Amp ldc_amp(u32 addr) { Amp v; @LDS_CLUSTER@ return v; }
-__device__ __forceinline__ void tr32(u32 (&a)[32])
-{
-  u32 m = 0x0000ffffu;
-#pragma unroll
-  for (int j = 16; j != 0; j >>= 1, m ^= (m << j)) {
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if (k & j) continue;
-      const u32 t = ((a[k] >> j) ^ a[k | j]) & m;
-      a[k | j] ^= t;
-      a[k] ^= t << j;
-    }
-  }
-}
-#define K @K@
-#define L @L@
-#define NH @NH@
-#define NREST @NREST@
-#define AB @B@
-#define BOX_BYTES @BOX@
-#define NT ((1 << (K - 1)) / 32)      /* consumer threads of one CTA */
-#define HALF ((size_t)AB << (K - 1))  /* bytes of one half tile */
-#define TABN ((NT * 33 + 7) / 8 * 8)
-__device__ __forceinline__ u64 tile_base(u64 t) { u64 b = 0; @TILEBASE@ return b; }
-__device__ __forceinline__ u64 deposit_high(u32 r) { u64 d = 0; @DEPHIGH@ return d; }
-__device__ __forceinline__ u64 deposit_rest(u32 r) { u64 d = 0; @DEPREST@ return d; }
-extern "C" __global__ void __launch_bounds__(NT + 64, 1)
-qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap tmap)
-{
-  extern __shared__ __align__(128) unsigned char smem[];
-  char *bufs = reinterpret_cast<char *>(smem);            // 2 stages x HALF
-  u64 *depo = reinterpret_cast<u64 *>(smem + 2 * HALF);
-  u16 *tabs = reinterpret_cast<u16 *>(depo + (1u << NH));
-  u64 *full = reinterpret_cast<u64 *>(tabs + TABN);
-  u64 *ready = full + 2;
-  u64 *empty = ready + 2;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const u32 rank = cluster_rank(), peer = rank ^ 1u;
-  for (u32 r = tid; r < (1u << NH); r += NT + 64) depo[r] = deposit_high(r);
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&ready[s], 1);
-      mbar_init(&empty[s], 2 * (NT / 32));
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  cluster_sync();  // the partner's barriers exist before anyone arrives on them
-  const u64 nclusters = gridDim.x / 2;
-  const u64 cid = blockIdx.x / 2;
-  const u64 per = (p.n_tiles + nclusters - 1) / nclusters;
-  const u64 begin = cid * per;
-  const u64 end = begin + per < p.n_tiles ? begin + per : p.n_tiles;
-  const u32 peer_bufs = peer_addr(sa(bufs), peer);
-  if (warp == NT / 32) {
-    // producer warp: this CTA's half of tile it into stage it % 2
-    for (u64 t = begin; t < end; ++t) {
-      const u32 it = (u32)(t - begin), s = it & 1u;
-      const bool ok = it < 2 || mbar_wait(&empty[s], ((it >> 1) - 1) & 1u, p.wait_limit);
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) atomicOr(p.err, 2);
-        break;
-      }
-      const u64 base = tile_base(t);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (lane == 0) mbar_expect(&full[s], (u32)HALF);
-      __syncwarp();
-      char *buf = bufs + HALF * s;
-      for (u32 q = lane; q < (1u << (NREST - 1)); q += 32) {
-        const u32 r = q | (rank << (NREST - 1));  // the copies whose top rest bit is this rank
-        const u64 g = base | deposit_rest(r);
-        @COORDS@
-        tma5(buf + (size_t)q * BOX_BYTES, &tmap, c0, c1, c2, c3, c4, &full[s]);
-      }
-    }
-  } else if (warp == NT / 32 + 1) {
-    // relay warp: once this half of a stage has landed, tell the partner
-    const u32 peer_ready = peer_addr(sa(ready), peer);
-    for (u64 t = begin; t < end; ++t) {
-      const u32 it = (u32)(t - begin), s = it & 1u;
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (it >> 1) & 1u, p.wait_limit))) {
-        if (lane == 0) atomicOr(p.err, 8);
-        break;
-      }
-      if (lane == 0) mbar_arrive_remote(peer_ready + 8u * s);
-      __syncwarp();
-    }
-  } else {
-    // consumer warps: sources of this CTA's outputs of the next tile while it
-    // loads, then both halves to global memory in coalesced runs
-    u16 *tab = tabs + warp * 32 * 33;
-    const u32 peer_empty = peer_addr(sa(empty), peer);
-    for (u64 t = begin; t < end; ++t) {
-      const u32 it = (u32)(t - begin), s = it & 1u;
-      const u64 base = tile_base(t);
-      {
-        const u32 j0 = (rank << (K - 1)) | ((u32)tid * 32u);
-@PLANES@
-@STEPS@
-@CHECK@
-        u32 r[32];
-@RLOCAL@
-        tr32(r);
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < 32; ++u) tab[lane * 33 + u] = (u16)r[u];
-        __syncwarp();
-      }
-      bool ok = mbar_wait(&full[s], (it >> 1) & 1u, p.wait_limit);
-      ok = ok && mbar_wait(&ready[s], (it >> 1) & 1u, p.wait_limit);
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) atomicOr(p.err, 1);
-        break;
-      }
-      const u32 own = sa(bufs) + (u32)(HALF * s), other = peer_bufs + (u32)(HALF * s);
-#pragma unroll 1
-      for (int e0 = 0; e0 < 32; e0 += 8) {
-        Amp v[8];
-        u64 g[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const u32 j = (rank << (K - 1)) | (((u32)warp * 32u + (u32)(e0 + u)) * 32u + (u32)lane);
-          const u32 src = tab[(e0 + u) * 33 + lane];
-          const u32 off = (src & ((1u << (K - 1)) - 1u)) * (u32)AB;
-          v[u] = (src >> (K - 1)) == rank ? lds_amp(own + off) : ldc_amp(other + off);
-          g[u] = base + depo[(j >> L) & ((1u << NH) - 1u)] + (j & ((1u << L) - 1u));
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          reinterpret_cast<Amp *>(p.state)[g[u]] = v[u];
-          if (p.probs) p.probs[g[u]] = AMP_PROB(v[u]);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&empty[s]);
-        mbar_arrive_remote(peer_empty + 8u * s);
-      }
-    }
-  }
-  __syncwarp();
-  cluster_sync();  // no CTA leaves while its partner may still read it
-}
-)QSIMSRC";
+
 
 void replace_all(std::string &s, const std::string &from, const std::string &to)
 {
@@ -646,21 +450,9 @@ uint32_t closed_stages(int amp, const TilePass &t)
     return st < 1 ? 1 : (uint32_t)st;
 }
 
-// A closed pass splits each tile over a cluster of two CTAs (two-stage
-// pipeline, half a tile each) when the layout enumerates at least one tile
-// bit by separate copies (the top one picks the half).
-bool closed_cluster(const TilePass &t) { return t.nrest >= 1 && t.k >= 11; }
-
 std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
 {
-    const bool cluster = closed_cluster(t);
-    std::string src = cluster ? kClosedClusterTemplate : kClosedTemplate;
-    replace_all(src, "@LDS_LOCAL@", amp == 16
-                ? "asm volatile(\"ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\" : \"=r\"(v.a), \"=r\"(v.b), \"=r\"(v.c), \"=r\"(v.d) : \"r\"(addr));"
-                : "asm volatile(\"ld.shared.v2.u32 {%0,%1}, [%2];\" : \"=r\"(v.a), \"=r\"(v.b) : \"r\"(addr));");
-    replace_all(src, "@LDS_CLUSTER@", amp == 16
-                ? "asm volatile(\"ld.shared::cluster.v4.u32 {%0,%1,%2,%3}, [%4];\" : \"=r\"(v.a), \"=r\"(v.b), \"=r\"(v.c), \"=r\"(v.d) : \"r\"(addr));"
-                : "asm volatile(\"ld.shared::cluster.v2.u32 {%0,%1}, [%2];\" : \"=r\"(v.a), \"=r\"(v.b) : \"r\"(addr));");
+    std::string src = kClosedTemplate;
     const std::vector<uint32_t> lb = tile_local_bits(t);
     const uint32_t K = t.k;
     std::vector<int> local_of(64, -1);
@@ -720,8 +512,7 @@ std::string generate_closed_source(uint32_t M, int amp, const qsim_step *steps, 
 
 std::vector<uint64_t> closed_key(uint32_t M, int amp, const qsim_step *steps, size_t n, const TilePass &t)
 {
-    std::vector<uint64_t> k = {0xC105EDull, M, (uint64_t)amp, t.k, t.l, t.nh, t.nrest, t.box_bytes, t.nout,
-                               closed_cluster(t) ? 2ull : 1ull};
+    std::vector<uint64_t> k = {0xC105EDull, M, (uint64_t)amp, t.k, t.l, t.nh, t.nrest, t.box_bytes, t.nout};
     for (uint32_t q = 0; q < t.nh; ++q) k.push_back(t.high[q]);
     for (uint32_t q = 0; q < t.nrest; ++q) k.push_back(t.rest_pos[q]);
     for (uint32_t q = 0; q < 6; ++q) k.push_back(t.tma_start[q]);
@@ -903,11 +694,6 @@ struct ClosedParams {
 
 size_t closed_smem_bytes(int amp, const TilePass &t)
 {
-    if (closed_cluster(t)) {
-        const size_t nt = ((size_t)1 << (t.k - 1)) / 32;
-        return 2 * ((size_t)amp << (t.k - 1)) + sizeof(uint64_t) * ((size_t)1 << t.nh) +
-               2 * ((nt * 33 + 7) / 8 * 8) + 6 * sizeof(uint64_t);
-    }
     const size_t nt = ((size_t)1 << t.k) / 32;
     const size_t tabn = (nt * 33 + 7) / 8 * 8;
     const size_t st = closed_stages(amp, t);
@@ -954,31 +740,12 @@ int launch_jit_closed(void *state, int amp, uint32_t M, const qsim_step *steps, 
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ClosedParams p{static_cast<char *>(state), d_probs, d_err, t.n_tiles, 1u << 24, 0u};
     void *args[] = {(void *)&p, (void *)tmap};
-    if (closed_cluster(t)) {
-        // one cluster of two CTAs (one per SM) per pair of SMs
-        const uint64_t pairs = (uint64_t)num_sms() / 2;
-        const unsigned grid = 2u * (unsigned)(t.n_tiles < pairs ? t.n_tiles : pairs);
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3((unsigned)((1u << (t.k - 1)) / 32 + 64));
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = static_cast<cudaStream_t>(stream);
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (ce == cudaSuccess) ce = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(e->kern), args);
-    } else {
-        const uint64_t cap = (uint64_t)num_sms();
-        const unsigned grid = (unsigned)(t.n_tiles < cap ? t.n_tiles : cap);
-        const unsigned block = (unsigned)((1u << t.k) / 32 + 32);
-        if (ce == cudaSuccess)
-            ce = cudaLaunchKernel(reinterpret_cast<const void *>(e->kern), dim3(grid), dim3(block), args, smem,
-                                  static_cast<cudaStream_t>(stream));
-    }
+    const uint64_t cap = (uint64_t)num_sms();
+    const unsigned grid = (unsigned)(t.n_tiles < cap ? t.n_tiles : cap);
+    const unsigned block = (unsigned)((1u << t.k) / 32 + 32);
+    if (ce == cudaSuccess)
+        ce = cudaLaunchKernel(reinterpret_cast<const void *>(e->kern), dim3(grid), dim3(block), args, smem,
+                              static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) {
         *msg = std::string("closed tile pass launch: ") + cudaGetErrorString(ce);
         return QSIM_ECUDA;
