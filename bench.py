@@ -62,7 +62,8 @@ UNIT = "amp-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 CSRC = os.path.join(ROOT, "paper_quant_ph_0308158_gb300", "csrc")
 # source files that define a kernel's code (every other kernel: kernels.cu)
-KERNEL_SOURCE = {"qsim_jit_gather": ("jit.cu", "prob_math.cuh")}
+KERNEL_SOURCE = {"qsim_jit_gather": ("jit.cu", "prob_math.cuh"), "qsim_jit_closed": ("jit.cu", "prob_math.cuh"),
+                 "qsim_jit_delta": ("jit.cu",)}
 KERNELS_CU = ("kernels.cu", "prob_math.cuh", "qsim_internal.h")
 
 
