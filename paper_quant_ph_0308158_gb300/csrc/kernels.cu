@@ -1246,6 +1246,28 @@ __global__ void __launch_bounds__(kThreads) probs_kernel(const char *__restrict_
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
+// complex64 probabilities without the norm: two amplitudes per 16-byte load
+// and two probabilities per 16-byte store, eight amplitudes in flight per
+// thread (the same arithmetic as probs_kernel, amplitude by amplitude).
+__global__ void __launch_bounds__(kThreads) probs_pairs_kernel(const uint4 *__restrict__ state,
+                                                               double2 *__restrict__ probs, uint64_t npairs)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; i + 3 * stride < npairs; i += 4 * stride) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(state + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            __stcs(probs + i + u * stride, make_double2(qsim_prob_bits(v[u].x, v[u].y), qsim_prob_bits(v[u].z, v[u].w)));
+    }
+    for (; i < npairs; i += stride) {
+        const uint4 v = __ldcs(state + i);
+        __stcs(probs + i, make_double2(qsim_prob_bits(v.x, v.y), qsim_prob_bits(v.z, v.w)));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restrict__ partials,
                                                           int n, double *__restrict__ out)
 {
@@ -1530,6 +1552,15 @@ int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const char *st = static_cast<const char *>(state);
+    if (!d_norm && amp_bytes == 8 && n >= 2 && d_probs) {  // complex64, probabilities only
+        const uint64_t np = n / 2;
+        const uint64_t want = (np + kThreads * 4 - 1) / (kThreads * 4);
+        const uint64_t cap = (uint64_t)num_sms() * 16;
+        const int grid = (int)(want < cap ? (want ? want : 1) : cap);
+        probs_pairs_kernel<<<grid, kThreads, 0, s>>>(reinterpret_cast<const uint4 *>(st),
+                                                     reinterpret_cast<double2 *>(d_probs), np);
+        return cudaGetLastError();
+    }
     if (!d_norm) {  // probabilities only: no accumulation, no reduction
         const uint64_t want = (n + kThreads * 4 - 1) / (kThreads * 4);
         const uint64_t cap = (uint64_t)num_sms() * 16;
