@@ -349,14 +349,16 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const u64 per = (p.n_tiles + gridDim.x - 1) / gridDim.x;
-  const u64 begin = (u64)blockIdx.x * per;
-  const u64 end = begin + per < p.n_tiles ? begin + per : p.n_tiles;
+  // tiles are dealt out cyclically: CTA b takes tiles b, b + grid, ...  At any
+  // moment the CTAs then work on consecutive tiles, whose short runs share
+  // DRAM pages.
+  const u64 cnt = blockIdx.x < p.n_tiles ? (p.n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (warp == NT / 32) {
     // producer warp: tile it goes to stage it % STAGES once that stage's
     // previous tile has been consumed
-    for (u64 t = begin; t < end; ++t) {
-      const u32 it = (u32)(t - begin), s = it % STAGES;
+    for (u64 i = 0; i < cnt; ++i) {
+      const u64 t = blockIdx.x + i * gridDim.x;
+      const u32 it = (u32)i, s = it % STAGES;
       if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1u, p.wait_limit)) {
         if (lane == 0) atomicOr(p.err, 2);
         return;
@@ -377,8 +379,9 @@ qsim_jit_closed(const __grid_constant__ Params p, const __grid_constant__ TMap t
   // consumer warps: sources of the next tile's outputs while it loads, then
   // shared memory to global memory in coalesced runs
   u16 *tab = tabs + warp * 32 * 33;
-  for (u64 t = begin; t < end; ++t) {
-    const u32 it = (u32)(t - begin), s = it % STAGES;
+  for (u64 i = 0; i < cnt; ++i) {
+    const u64 t = blockIdx.x + i * gridDim.x;
+    const u32 it = (u32)i, s = it % STAGES;
     const u64 base = tile_base(t);
     {
       const u32 j0 = (u32)tid * 32u;

@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(char *__restrict__ stat
 // tiles with the same active set.
 constexpr int kTileThreads = 512;
 constexpr int kMaxOutBits = 40;
+constexpr uint32_t kProductStages = 4;            // stages of a product-input tile pass
+constexpr size_t kMaxTileSmem = 227 * 1024;       // dynamic shared memory of one CTA
 constexpr int kMaskWords = kMaxTileSteps / 32;
 
 struct TileKParams {
@@ -190,6 +192,7 @@ struct TileKParams {
     int *err;
     uint64_t n_tiles;
     uint32_t k, l, nh, nsteps, all_local, stages, nout;
+    uint32_t buf_bytes;            // stage region: tiles, or the product tables
     uint32_t high[kMaxHighBits];
     uint32_t outpos[kMaxOutBits];  // global bit of tile-id bit q
     uint32_t tma, nrest, epa, box_bytes;
@@ -202,6 +205,8 @@ struct TileKParams {
     // loaded.  qtab: per address bit b, (q_b(0), q_b(1)) as FP64 complex;
     // plow: the product over the tile's low l bits for each of their 2^l
     // values; phigh: over its high bits for each of their 2^nh values.
+    // The stage region then holds those two tables and, per stage, the
+    // tile's products over its high bits (written by the producer warp).
     const double2 *qtab, *plow, *phigh;
 };
 
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     const uint32_t tile_amps = 1u << p.k;
     const size_t tile_bytes = (size_t)B * tile_amps;
     char *bufs = reinterpret_cast<char *>(smem);
-    uint64_t *depo = reinterpret_cast<uint64_t *>(smem + tile_bytes * p.stages);
+    uint64_t *depo = reinterpret_cast<uint64_t *>(smem + p.buf_bytes);
     TileStageMeta *meta = reinterpret_cast<TileStageMeta *>(depo + (1u << p.nh));
     uint64_t *full = reinterpret_cast<uint64_t *>(meta + p.stages);
     uint64_t *empty = full + p.stages;
@@ -367,6 +372,16 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     }
     for (uint32_t i = tid; i < p.nsteps; i += nthreads) steps_sm[i] = p.steps[i];
     for (uint32_t i = tid; i < kMaxOutBits; i += nthreads) outpos[i] = p.outpos[i];
+    // product input: the stage region holds the products over the low bits,
+    // over the high bits, and per stage the tile's scaled high products
+    using PT = typename ProdT<B>::T;
+    PT *tlow = reinterpret_cast<PT *>(bufs);
+    PT *phigh = tlow + (1u << p.l);
+    PT *thigh = phigh + (1u << p.nh);  // + stage * 2^nh
+    if (PRODUCT) {
+        for (uint32_t u = tid; u < (1u << p.l); u += nthreads) tlow[u] = ProdT<B>::of(p.plow[u]);
+        for (uint32_t h = tid; h < (1u << p.nh); h += nthreads) phigh[h] = ProdT<B>::of(p.phigh[h]);
+    }
     if (tid == 0) {
         for (uint32_t s = 0; s < p.stages; ++s) {
             mbar_init(&full[s], 1);
@@ -432,7 +447,28 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                 if (lane == 0) mbar_arrive(&full[s]);  // end marker, no bytes
                 return;
             }
-            if (PRODUCT) {  // nothing to load: the consumers compute the sources
+            if (PRODUCT) {
+                // nothing to load: the tile's factor over the bits outside it
+                // (FP64, a butterfly product over the lanes, which leaves the
+                // same value in every lane since each complex product is
+                // commutative bit for bit), then its products over the high
+                // tile bits (complex64: in float-float) for the consumers
+                double2 f = make_double2(1.0, 0.0);
+                if ((uint32_t)lane < p.nout) {
+                    const uint32_t b = outpos[lane];
+                    f = p.qtab[2 * b + (uint32_t)((base >> b) & 1ull)];
+                }
+#pragma unroll
+                for (int off = 16; off; off >>= 1) {
+                    double2 g;
+                    g.x = __shfl_xor_sync(0xffffffffu, f.x, off);
+                    g.y = __shfl_xor_sync(0xffffffffu, f.y, off);
+                    f = dcmul(f, g);
+                }
+                const PT c = ProdT<B>::of(f);
+                PT *th = thigh + ((size_t)s << p.nh);
+                for (uint32_t h = lane; h < (1u << p.nh); h += 32) th[h] = ProdT<B>::scale(c, phigh[h]);
+                __syncwarp();
                 if (lane == 0) mbar_arrive(&full[s]);
                 continue;
             }
@@ -469,17 +505,6 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
     bool have_perm = false;  // perm holds the table of an earlier tile
     uint32_t c0 = 0, delta = 0;  // affine passes: image of 0 in that table, shift now
     A *st = reinterpret_cast<A *>(p.state);
-    // product input: the tile buffers are free, so they hold the per-tile
-    // products over the high bits (2^nh) and the products over the low bits
-    using PT = typename ProdT<B>::T;
-    PT *thigh = reinterpret_cast<PT *>(bufs);
-    PT *tlow = thigh + (1u << p.nh);
-    PT *phigh = tlow + (1u << p.l);
-    PT *tfac = phigh + (1u << p.nh);
-    if (PRODUCT) {
-        for (uint32_t u = tid; u < (1u << p.l); u += kTileThreads) tlow[u] = ProdT<B>::of(p.plow[u]);
-        for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) phigh[h] = ProdT<B>::of(p.phigh[h]);
-    }
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % p.stages;
         if (!mbar_wait_bounded(&full[s], (it / p.stages) & 1u, p.wait_limit)) {
@@ -541,32 +566,8 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
             have_perm = true;
             consumer_sync();  // the new table is complete
         }
-        if (PRODUCT) {
-            // this tile's factor over the bits outside it (FP64, a butterfly
-            // product over the lanes of warp 0), then its products over the
-            // high tile bits (complex64: in float-float)
-            consumer_sync();  // everyone is done with the previous tile's products
-            if (warp == 0) {
-                double2 f = make_double2(1.0, 0.0);
-                if ((uint32_t)lane < p.nout) {
-                    const uint32_t b = p.outpos[lane];
-                    f = p.qtab[2 * b + (uint32_t)((base >> b) & 1ull)];
-                }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) {
-                    double2 g;
-                    g.x = __shfl_xor_sync(0xffffffffu, f.x, off);
-                    g.y = __shfl_xor_sync(0xffffffffu, f.y, off);
-                    f = dcmul(f, g);
-                }
-                if (lane == 0) *tfac = ProdT<B>::of(f);
-            }
-            consumer_sync();
-            const PT c = *tfac;
-            for (uint32_t h = tid; h < (1u << p.nh); h += kTileThreads) thigh[h] = ProdT<B>::scale(c, phigh[h]);
-            consumer_sync();
-        }
         const A *buf = reinterpret_cast<const A *>(bufs + tile_bytes * s);
+        const PT *th = thigh + ((size_t)s << p.nh);
         for (uint32_t j0 = 0; j0 < tile_amps; j0 += kTileThreads * 4) {
             A v[4];
 #pragma unroll
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(kTileThreads + 32, 1)
                 if (j < tile_amps) {
                     if (PRODUCT) {
                         const uint32_t src = idle ? j : ((uint32_t)perm[j] ^ delta);
-                        v[e] = ProdT<B>::mul(thigh[src >> p.l], tlow[src & lmask]);
+                        v[e] = ProdT<B>::mul(th[src >> p.l], tlow[src & lmask]);
                     } else {
                         v[e] = buf[perm[j] ^ delta];
                     }
@@ -1337,12 +1338,31 @@ static uint32_t tile_stages(int amp_bytes, int k)
     return 1;
 }
 
+// Stage region of a product-input pass: the products over the low bits and
+// over the high bits, and the tile's scaled high products per stage (16 bytes
+// an entry for both amplitude types), rounded to 128 bytes.
+static size_t product_region_bytes(uint32_t l, uint32_t nh)
+{
+    const size_t b = 16 * (((size_t)1 << l) + ((size_t)1 << nh) * (1 + kProductStages));
+    return (b + 127) / 128 * 128;
+}
+
+static size_t tile_smem_for(size_t region, uint32_t st, int k)
+{
+    return region + sizeof(uint64_t) * (1u << kMaxHighBits) + sizeof(TileStageMeta) * st +
+           2 * sizeof(uint64_t) * st + sizeof(TileStep) * kMaxTileSteps + sizeof(uint32_t) * kMaxOutBits +
+           sizeof(uint16_t) * ((size_t)1 << k);
+}
+
 size_t tile_smem_bytes(int amp_bytes, int k)
 {
     const uint32_t st = tile_stages(amp_bytes, k);
-    return ((size_t)amp_bytes << k) * st + sizeof(uint64_t) * (1u << kMaxHighBits) +
-           sizeof(TileStageMeta) * st + 2 * sizeof(uint64_t) * st + sizeof(TileStep) * kMaxTileSteps +
-           sizeof(uint32_t) * kMaxOutBits + sizeof(uint16_t) * ((size_t)1 << k);
+    return tile_smem_for(((size_t)amp_bytes << k) * st, st, k);
+}
+
+bool tile_product_fits(const TilePass &t)
+{
+    return tile_smem_for(product_region_bytes(t.l, t.nh), kProductStages, (int)t.k) <= kMaxTileSmem;
 }
 
 int encode_tile_map(void *state, const TilePass &t, void *map128)
@@ -1382,7 +1402,9 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
     p.nh = t.nh;
     p.nsteps = t.nsteps;
     p.all_local = t.all_local;
-    p.stages = tile_stages(amp_bytes, (int)t.k);
+    // a product-input pass loads nothing: its stages hold small tables only
+    p.stages = prod ? kProductStages : tile_stages(amp_bytes, (int)t.k);
+    p.buf_bytes = (uint32_t)(prod ? product_region_bytes(t.l, t.nh) : ((size_t)amp_bytes << t.k) * p.stages);
     p.nout = t.nout;
     for (int i = 0; i < kMaxHighBits; ++i) p.high[i] = t.high[i];
     for (int i = 0; i < kMaxOutBits; ++i) p.outpos[i] = i < (int)t.nout ? t.outpos[i] : 0u;
@@ -1400,7 +1422,8 @@ int launch_tile(void *state, int amp_bytes, const TilePass &t, const TileStep *d
         if (te == 1) p.tma = 0;  // no driver entry point: one bulk copy per run
         else if (te != 0) return cudaErrorInvalidValue;
     }
-    const size_t smem = tile_smem_bytes(amp_bytes, (int)t.k);
+    if (prod && !tile_product_fits(t)) return cudaErrorInvalidValue;
+    const size_t smem = prod ? tile_smem_for(p.buf_bytes, p.stages, (int)t.k) : tile_smem_bytes(amp_bytes, (int)t.k);
     const uint64_t cap = (uint64_t)num_sms();
     const int grid = (int)(t.n_tiles < cap ? t.n_tiles : cap);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1552,7 +1575,10 @@ int launch_probabilities(const void *state, int amp_bytes, uint64_t n, double *d
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const char *st = static_cast<const char *>(state);
-    if (!d_norm && amp_bytes == 8 && n >= 2 && d_probs) {  // complex64, probabilities only
+    // complex64, probabilities only, both buffers on 16-byte boundaries (a
+    // caller's d_probs need only be 8-byte aligned)
+    if (!d_norm && amp_bytes == 8 && n >= 2 && n % 2 == 0 && d_probs &&
+        (reinterpret_cast<uintptr_t>(st) & 15u) == 0 && (reinterpret_cast<uintptr_t>(d_probs) & 15u) == 0) {
         const uint64_t np = n / 2;
         const uint64_t want = (np + kThreads * 4 - 1) / (kThreads * 4);
         const uint64_t cap = (uint64_t)num_sms() * 16;

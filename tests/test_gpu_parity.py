@@ -501,6 +501,27 @@ def test_apply_circuit_probabilities_rejects_bad_output(cuda):
             sim.apply_probabilities(W.cnot_circuit(8, 4, 1), buf.data_ptr() + 4)
 
 
+def test_complex64_probabilities_any_8_byte_offset(cuda):
+    """complex64 probabilities into a buffer on a 16-byte boundary and one 8
+    bytes past it (the 16-byte pair stores are used only where both buffers
+    allow them): bit-identical to the oracle either way, nothing written
+    outside the 2^M entries."""
+    torch = cuda
+    for M in (1, 5, 16):
+        k1 = W.random_state(M, np.complex64, 21 + M)
+        want = oracle.probabilities(k1)
+        buf = torch.full((2 + (1 << M) + 2,), -1.0, dtype=torch.float64, device="cuda")
+        for off in (2, 1):   # 16-byte and 8-byte aligned starts
+            buf.fill_(-1.0)
+            with Simulator(M, np.complex64) as sim:
+                sim.load_state(k1)
+                sim.apply_probabilities(W.make_steps([]), buf.data_ptr() + 8 * off)
+                sim.synchronize()
+            got = buf.cpu().numpy()
+            np.testing.assert_array_equal(got[off:off + (1 << M)].view(np.uint64), want.view(np.uint64))
+            assert (got[:off] == -1.0).all() and (got[off + (1 << M):] == -1.0).all()
+
+
 def test_wide_indices_m33():
     """M = 33 complex64 (64 GiB + 64 GiB scratch): 64-bit index paths of the
     compiled, bit-sliced, affine, tile and sweep kernels, checked on sampled
