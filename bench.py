@@ -86,6 +86,8 @@ def workload(name: str):
         return W.config_hybrid(28)
     if name == "parity_m32":  # Sec. 4 example, input generated on the device (App. 1)
         return W.config_parity(32)
+    if name == "parity_m28":  # 2 GiB: the small case for product-input captures
+        return W.config_parity(28)
     raise SystemExit("unknown workload " + name)
 
 
@@ -1071,7 +1073,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "cnot_m26", "parity_m32", "hybrid_m28",
+    ap.add_argument("--workload", default="adder_m32", choices=["mixed_m28", "adder_m32", "adder_m28", "cnot_m16", "mixed_m24", "cnot_m28", "cnot_m26", "parity_m32", "parity_m28", "hybrid_m28",
                              "batch_cnot", "batch_mixed", "serve", "parity_scan", "gather_floor"])
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--tile-bits", type=int, default=0, help="tile width k (0: default)")

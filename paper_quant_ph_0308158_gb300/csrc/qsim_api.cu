@@ -530,11 +530,8 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     fill_stats(plan, c->M, c->amp, &c->stats);
     // product input (App. 1): a first tile pass computes its sources from the
     // qubits; any other plan starts from the state written out first
-    // (its product tables live in the tile buffers: they must fit one tile)
     const bool fuse_input = qubits && !plan.passes.empty() && plan.passes[0].kind == kTile &&
-                            !plan.passes[0].tile.closed &&
-                            (32ull << plan.passes[0].tile.nh) + (16ull << plan.passes[0].tile.l) + 16 <=
-                                ((uint64_t)c->amp << plan.passes[0].tile.k);
+                            !plan.passes[0].tile.closed && tile_product_fits(plan.passes[0].tile);
     if (qubits && !fuse_input) {
         rc = qsim_load_product_state(c, qubits);
         if (rc != QSIM_OK) return rc;

@@ -248,6 +248,8 @@ int sliced_steps_of(uint32_t M, const qsim_step *steps, size_t L, std::vector<Sl
 int launch_batch_level(int amp_bytes, bool wide, const BatchPass *d_passes, const BatchItem *d_items,
                        uint32_t n_items, uint32_t *d_counter, size_t smem, void *stream);
 size_t tile_smem_bytes(int amp_bytes, int k);
+// Whether a product-input (App. 1) tile pass with this layout fits in shared memory.
+bool tile_product_fits(const TilePass &t);
 // The tensor map (128 bytes) of a tile layout over a state: 0 on success, 1
 // without the driver's encoder, 2 when the driver rejects the layout.
 int encode_tile_map(void *state, const TilePass &t, void *map128);
