@@ -731,7 +731,7 @@ constexpr double kEffRandom = 0.50;
 constexpr double kSlicedStepS = 2.8e-14;  // per step and output, interpreter
 constexpr double kCompiledStepS = 2.2e-15; // per step and output, compiled kernel
 constexpr double kLaunchS = 4e-6;
-constexpr double kEffClosed = 0.75;        // closed pass: tile streaming with 64-byte runs
+constexpr double kEffClosed = 0.92;        // closed pass: tiles dealt cyclically, 64-byte runs
 constexpr double kTableStepS = 2.1e-11;    // tile table build, per local index and step, one SM
 constexpr double kSms = 152.0;
 constexpr double kClosedStepS = 1.2e-15;   // per step and output, planes in registers
@@ -753,7 +753,7 @@ double pass_cost_s(const Pass &p, uint32_t M, size_t amp)
         // sources are found while it loads)
         const double mem = p.alg_bytes / (kEffClosed * kPeakBytesPerS);
         const double alu = (double)p.tile.jit_n * (double)(1ull << M) * kClosedStepS;
-        return kLaunchS + std::max(mem, alu) + 0.25 * std::min(mem, alu);
+        return kLaunchS + std::max(mem, alu) + 0.1 * std::min(mem, alu);
     }
     if (p.kind == kTile) {
         // table builds: every local index through every step, by the SMs
