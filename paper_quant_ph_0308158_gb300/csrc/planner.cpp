@@ -1068,6 +1068,12 @@ double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp) { return 1e3 
 
 double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp) { return 1e3 * pass_cost_s(p, M, amp); }
 
+double product_state_estimated_ms(uint32_t M, size_t amp)
+{
+    // one write of the state, streamed like a tile pass
+    return 1e3 * (kLaunchS + (double)(1ull << M) * (double)amp / (kEffTile * kPeakBytesPerS));
+}
+
 std::vector<double> product_tables(uint32_t M, const double *qubits, const TilePass &t)
 {
     // complex products with each real product and sum rounded separately

@@ -527,6 +527,24 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     }
     rc = make_plan(c->M, steps, L, o, &plan, &msg);
     if (rc != QSIM_OK) return fail(rc, msg);
+    if (qubits && o.closed_known) {
+        // a closed pass cannot generate the product input (App. 1), a first
+        // tile pass can: weigh the plan without closed passes too, charging
+        // a plan that cannot take the input its own product-state pass
+        const auto takes_input = [](const Plan &p) {
+            return !p.passes.empty() && p.passes[0].kind == kTile && !p.passes[0].tile.closed &&
+                   tile_product_fits(p.passes[0].tile);
+        };
+        const auto cost = [&](const Plan &p) {
+            return plan_estimated_ms(p, c->M, c->amp) +
+                   (takes_input(p) ? 0.0 : product_state_estimated_ms(c->M, c->amp));
+        };
+        PlanOptions o2 = o;
+        o2.closed_known = false;
+        Plan alt;
+        std::string amsg;
+        if (make_plan(c->M, steps, L, o2, &alt, &amsg) == QSIM_OK && cost(alt) < cost(plan)) plan = std::move(alt);
+    }
     fill_stats(plan, c->M, c->amp, &c->stats);
     // product input (App. 1): a first tile pass computes its sources from the
     // qubits; any other plan starts from the state written out first

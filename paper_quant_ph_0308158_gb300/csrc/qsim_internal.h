@@ -175,6 +175,8 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
 // The cost model's estimated device time of a plan / one pass (planner.cpp).
 double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp);
 double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp);
+// Estimated time of writing an App. 1 product state on its own.
+double product_state_estimated_ms(uint32_t M, size_t amp);
 
 // One circuit's pass inside a batched launch (batch.cu builds them).
 struct BatchPass {
