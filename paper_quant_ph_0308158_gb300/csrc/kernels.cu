@@ -1168,38 +1168,46 @@ __device__ __forceinline__ double2 partial_product(const double2 *q, uint64_t i,
     return acc;
 }
 
-constexpr int kProductLowBits = 10;  // table of low-bit partial products in shared memory
+constexpr int kProductLowBits = 10;   // low-bit partial products: one table per CTA
+constexpr int kProductGroupBits = 8;  // high bits in three groups of up to 8: three tables
 
-// k1(i) = (product over the high bits) x (product over the low h bits): the
-// low-bit partial products of the whole state fit one 2^h table, and each
-// CTA computes the high-bit partial product of its range once.
+// k1(i) = (product over the high bits) x (product over the low h bits).  Each
+// CTA tabulates the low-bit partial products (2^h) and the partial products
+// of three groups of high bits (2^8 each) in FP64, kept as ProdT (complex64:
+// float-float, so the per-amplitude work is FP32; complex128: FP64).  Each
+// warp takes runs of 2^h consecutive amplitudes: the run's high product is
+// two table products, then every amplitude one product with the low table.
 template <int B>
 __global__ void __launch_bounds__(kThreads) product_state_kernel(char *__restrict__ state,
                                                                  const double *__restrict__ qubits,
                                                                  uint32_t M, uint64_t n)
 {
+    using PT = typename ProdT<B>::T;
     __shared__ double2 q[2 * QSIM_MAX_QUBITS];
-    __shared__ double2 lo_tab[1 << kProductLowBits];
-    __shared__ double2 hi_val;
+    __shared__ PT lo_tab[1 << kProductLowBits];
+    __shared__ PT grp[3][1 << kProductGroupBits];
     const int h = M < (uint32_t)kProductLowBits ? (int)M : kProductLowBits;
     for (uint32_t j = threadIdx.x; j < 2 * M; j += kThreads)
         q[j] = make_double2(qubits[2 * j], qubits[2 * j + 1]);
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < (1u << h); j += kThreads) lo_tab[j] = partial_product(q, j, 0, h);
-    // each CTA covers whole runs of 2^h consecutive indices (one high value each)
+    for (uint32_t j = threadIdx.x; j < (1u << h); j += kThreads) lo_tab[j] = ProdT<B>::of(partial_product(q, j, 0, h));
+    for (uint32_t e = threadIdx.x; e < 3u << kProductGroupBits; e += kThreads) {
+        const int g = (int)(e >> kProductGroupBits);
+        const uint32_t j = e & ((1u << kProductGroupBits) - 1u);
+        const int lo = h + kProductGroupBits * g;
+        const int hi = lo + kProductGroupBits < (int)M ? lo + kProductGroupBits : (int)M;
+        grp[g][j] = ProdT<B>::of(lo < hi ? partial_product(q, (uint64_t)j << lo, lo, hi) : make_double2(1.0, 0.0));
+    }
+    __syncthreads();
+    const uint32_t warps = kThreads / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint64_t runs = n >> h;
-    for (uint64_t r = blockIdx.x; r < runs; r += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) hi_val = (int)M > h ? partial_product(q, r << h, h, (int)M) : make_double2(1.0, 0.0);
-        __syncthreads();
-        const double2 hv = hi_val;
-        for (uint32_t j = threadIdx.x; j < (1u << h); j += kThreads) {
-            const double2 v = (int)M > h ? cmul_rn(hv, lo_tab[j]) : lo_tab[j];
-            const uint64_t i = (r << h) | j;
-            if (B == 16)
-                reinterpret_cast<double2 *>(state)[i] = v;
-            else
-                reinterpret_cast<float2 *>(state)[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    const uint32_t gm = (1u << kProductGroupBits) - 1u;
+    for (uint64_t r = (uint64_t)blockIdx.x * warps + warp; r < runs; r += (uint64_t)gridDim.x * warps) {
+        PT hv = ProdT<B>::scale(grp[0][r & gm], grp[1][(r >> kProductGroupBits) & gm]);
+        hv = ProdT<B>::scale(hv, grp[2][(r >> (2 * kProductGroupBits)) & gm]);
+        for (uint32_t j = lane; j < (1u << h); j += 32) {
+            auto v = ProdT<B>::mul(hv, lo_tab[j]);
+            reinterpret_cast<decltype(v) *>(state)[(r << h) | j] = v;
         }
     }
 }
@@ -1649,9 +1657,11 @@ int launch_product_state(void *state, int amp_bytes, uint32_t M, const double *d
 {
     const uint64_t n = 1ull << M;
     const int h = M < (uint32_t)kProductLowBits ? (int)M : kProductLowBits;
+    if ((int)M > h + 3 * kProductGroupBits) return cudaErrorInvalidValue;
     const uint64_t runs = n >> h;
+    const uint64_t warps = (runs + kThreads / 32 - 1) / (kThreads / 32);
     const uint64_t cap = (uint64_t)num_sms() * 8;
-    const int grid = (int)(runs < cap ? runs : cap);
+    const int grid = (int)(warps < cap ? warps : cap);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (amp_bytes == 8)
         product_state_kernel<8><<<grid, kThreads, 0, s>>>(static_cast<char *>(state), d_qubits, M, n);

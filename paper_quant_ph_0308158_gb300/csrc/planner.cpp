@@ -1068,10 +1068,26 @@ double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp) { return 1e3 
 
 double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp) { return 1e3 * pass_cost_s(p, M, amp); }
 
+// App. 1 input, per amplitude: the product-state kernel (complex64: one
+// float-float complex product; complex128: one FP64 complex product), and a
+// first tile pass that generates its sources (a product from two tables) and
+// writes the probabilities, which is bound by instruction issue, not HBM.
+constexpr double kProductOutS[2] = {1.3e-12, 1.1e-11};       // complex64, complex128
+constexpr double kProductFusedOutS[2] = {5.5e-12, 1.4e-11};
+
 double product_state_estimated_ms(uint32_t M, size_t amp)
 {
-    // one write of the state, streamed like a tile pass
-    return 1e3 * (kLaunchS + (double)(1ull << M) * (double)amp / (kEffTile * kPeakBytesPerS));
+    const double n = (double)(1ull << M);
+    const double write = n * (double)amp / (kEffTile * kPeakBytesPerS);
+    return 1e3 * (kLaunchS + std::max(write, n * kProductOutS[amp == 16]));
+}
+
+double product_plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp, bool fused)
+{
+    if (!fused || plan.passes.empty()) return plan_estimated_ms(plan, M, amp) + product_state_estimated_ms(M, amp);
+    const double first = pass_cost_s(plan.passes[0], M, amp);
+    const double gen = kLaunchS + (double)(1ull << M) * kProductFusedOutS[amp == 16];
+    return 1e3 * (plan_cost_s(plan, M, amp) - first + std::max(first, gen));
 }
 
 std::vector<double> product_tables(uint32_t M, const double *qubits, const TilePass &t)

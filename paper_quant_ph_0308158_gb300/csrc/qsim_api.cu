@@ -530,15 +530,13 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     if (qubits && o.closed_known) {
         // a closed pass cannot generate the product input (App. 1), a first
         // tile pass can: weigh the plan without closed passes too, charging
-        // a plan that cannot take the input its own product-state pass
+        // a plan that cannot take the input its own product-state pass and
+        // one that can the per-amplitude cost of generating it
         const auto takes_input = [](const Plan &p) {
             return !p.passes.empty() && p.passes[0].kind == kTile && !p.passes[0].tile.closed &&
                    tile_product_fits(p.passes[0].tile);
         };
-        const auto cost = [&](const Plan &p) {
-            return plan_estimated_ms(p, c->M, c->amp) +
-                   (takes_input(p) ? 0.0 : product_state_estimated_ms(c->M, c->amp));
-        };
+        const auto cost = [&](const Plan &p) { return product_plan_estimated_ms(p, c->M, c->amp, takes_input(p)); };
         PlanOptions o2 = o;
         o2.closed_known = false;
         Plan alt;
@@ -606,14 +604,10 @@ static int apply_impl(qsim_ctx *c, const qsim_step *steps, size_t L, double *d_p
     bool fused = false;
     for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
         const Pass &p = plan.passes[pi];
-        // the last pass writes the probabilities when its kernel can
-        // (not a closed pass: its source evaluation already fills the SMs'
-        // issue slots, and the FP64 sums run faster as their own streaming
-        // pass -- 15.2 + 13.0 ms against 30.3 ms fused on the M = 32 adder)
-        double *pp = (d_probs && pi + 1 == plan.passes.size() && p.kind != kSweep &&
-                      !(p.kind == kTile && p.tile.closed))
-                         ? d_probs
-                         : nullptr;
+        // the last pass writes the probabilities when its kernel can (every
+        // kind but a sweep; on the M = 32 adder the closed pass writing them
+        // took 18.5 ms against 11.8 + 11.7 ms for a separate pass)
+        double *pp = (d_probs && pi + 1 == plan.passes.size() && p.kind != kSweep) ? d_probs : nullptr;
         double bytes = (pi == 0 && fuse_input) ? n * c->amp : p.alg_bytes;  // product input: writes only
         if (pp) {
             // every tile is read; touched tiles are written; plus the probabilities

@@ -175,8 +175,11 @@ int make_plan(uint32_t M, const qsim_step *steps, size_t L, const PlanOptions &o
 // The cost model's estimated device time of a plan / one pass (planner.cpp).
 double plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp);
 double pass_estimated_ms(const Pass &p, uint32_t M, size_t amp);
-// Estimated time of writing an App. 1 product state on its own.
+// Estimated time of writing an App. 1 product state on its own, and of a
+// plan applied to such an input: generated by its first (tile) pass when
+// fused, else written first by its own pass.
 double product_state_estimated_ms(uint32_t M, size_t amp);
+double product_plan_estimated_ms(const Plan &plan, uint32_t M, size_t amp, bool fused);
 
 // One circuit's pass inside a batched launch (batch.cu builds them).
 struct BatchPass {

@@ -91,8 +91,8 @@ def test_closed_pass_writes_probabilities(cuda, dtype):
     p = torch.full((1 << M,), -1.0, dtype=torch.float64, device="cuda")
     got, kernels = _run_closed(M, dtype, steps, k1, probs=p)
     np.testing.assert_array_equal(got, want)
-    # a closed pass leaves the probabilities to their own streaming pass
-    assert kernels == ["qsim_jit_closed", "probs_kernel"]
+    # the closed pass writes the probabilities beside the amplitudes it stores
+    assert kernels == ["qsim_jit_closed"]
     want_p = oracle.probabilities(want)
     if dtype == np.complex64:
         np.testing.assert_array_equal(p.cpu().numpy().view(np.uint64), want_p.view(np.uint64))

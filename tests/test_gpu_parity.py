@@ -319,9 +319,9 @@ def test_adder_m32_workload_sampled():
 def test_adder_m32_benchmarked_closed_pass_sampled():
     """M=32 complex64 adder in place as benchmarked: compiled kernels on, so
     the whole circuit is one closed tile pass (its net map changes only
-    b_4..b_14 and the carry-out), then the probabilities' own pass."""
+    b_4..b_14 and the carry-out), which also writes the probabilities."""
     st, kernels = _sampled_check(W.config_adder_m32(), "inplace", rows=1 << 20, jit=True, probs=True)
-    assert st["passes"] == 1 and kernels == ["qsim_jit_closed", "probs_kernel"]
+    assert st["passes"] == 1 and kernels == ["qsim_jit_closed"]
 
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
