@@ -359,16 +359,14 @@ def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, s
     r = Resident()
     M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
     n = 1 << M
+    tdt = torch.complex64 if dtype == np.complex64 else torch.complex128
     # seeded state in pinned host memory (also the e2e input buffer), or the
     # qubits of a product-state input generated on the device (App. 1); the
     # end-to-end leg copies that state in from the host all the same
     qubits = cfg.get("qubits")
-    h_in = h_in_buf = None
+    h_in = None
     if qubits is None or (for_e2e and not args.no_e2e):
-        # page-locked through the library, in chunks that copy at the link rate
-        from paper_quant_ph_0308158_gb300 import HostBuffer
-        h_in_buf = HostBuffer((n,), dtype)
-        h_in = h_in_buf.array
+        h_in = torch.empty(n, dtype=tdt, pin_memory=True).numpy()
         if qubits is None:
             W.random_state(M, dtype, cfg["state_seed"], out=h_in)
         else:  # the only product-state workload is the Sec. 4 alternating input
@@ -446,29 +444,26 @@ def measure_resident(args, cfg, strategy, use_jit, local, ws, steps_k, warmup, s
     r.roofline, r.kernel_ms, r.kernel_launches = _roofline(passes, cfg["name"])
     r.launches = len(passes)  # every pass kernel and probabilities kernel in the timed region
     r.sim, r.h_in, r.qubits, r.scratch, r.jit_ms, r.tuned, r.probs = sim, h_in, qubits, scratch, jit_ms, tuned, probs
-    r.h_in_buf = h_in_buf
     r.jit = bool(use_jit)
     return r
 
 
 def measure_e2e(args, cfg, r, local, ws, steps_k):
     """The same metric end to end through the C ABI with host buffers: each
-    step copies its state in from page-locked host memory, applies the circuit
-    and copies the FP64 probabilities out to page-locked host memory (both
-    from qsim_host_alloc).  Two contexts on two streams alternate steps, so one
-    step's copies overlap the other's kernels (each context waits for its
-    previous step before reusing its buffers); copies in go one after the
-    other over the host link, and so do copies out (one shared copy stream)."""
+    step copies its state in from pinned host memory, applies the circuit and
+    copies the FP64 probabilities out to pinned host memory.  Two contexts on
+    two streams alternate steps, so one step's copies overlap the other's
+    kernels (each context waits for its previous step before reusing its
+    buffers); copies in go one after the other over the host link."""
     import torch
-    from paper_quant_ph_0308158_gb300 import HostBuffer, Simulator
+    from paper_quant_ph_0308158_gb300 import Simulator
 
     M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
     n = 1 << M
     L = len(steps)
-    outs_buf = HostBuffer((2, n), np.float64)
+    outs_block = torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
     stream = torch.cuda.current_stream()
     s2 = torch.cuda.Stream()
-    copies_out = torch.cuda.Stream()
     with torch.cuda.stream(s2):
         sim2 = Simulator(M, dtype, scratch=r.scratch)
     sim2.set_strategy(args.strategy or strategy_for(args.workload), args.tile_bits, args.low_bits)
@@ -476,10 +471,8 @@ def measure_e2e(args, cfg, r, local, ws, steps_k):
     if r.jit:
         sim2.set_jit(True)
     sims = (r.sim, sim2)
-    for sm in sims:
-        sm.set_copy_stream(copies_out.cuda_stream)
     streams = (stream, s2)
-    outs = [outs_buf.array[0], outs_buf.array[1]]
+    outs = [outs_block[:n].numpy(), outs_block[n:].numpy()]
     loaded = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_step(i):
@@ -513,15 +506,11 @@ def measure_e2e(args, cfg, r, local, ws, steps_k):
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(max(f0.elapsed_time(e) for e in ends), ws)
     sim2.close()
-    r.sim.set_copy_stream(0)
-    del outs
-    outs_buf.close()
+    del outs, outs_block
     return {"value": ws * n * L * ke / (ms_e2e * 1e-3), "unit": UNIT,
             "h2d_bytes_per_step": n * dtype.itemsize, "d2h_bytes_per_step": n * 8,
             "ms_per_step": ms_e2e / ke, "steps": ke,
-            "pipelining": "two contexts on two streams alternate steps; copies in are serialised, "
-                          "and so are copies out (one shared copy stream)",
-            "host_buffers": "qsim_host_alloc (1 GiB chunks kept where they copy at the link rate)"}
+            "pipelining": "two contexts on two streams alternate steps; copies in are serialised"}
 
 
 def cpu_baseline_for(args, cfg, h_in):
@@ -571,8 +560,6 @@ def run_ours(args, rank, ws, local):
     h_in_bytes = 0 if r.h_in is None else r.h_in.nbytes
     r.sim.close()
     r.h_in = None
-    if r.h_in_buf is not None:
-        r.h_in_buf.close()
     del r.probs
 
     # ---- the other single-circuit workload, on the same line ------------------
@@ -959,21 +946,22 @@ def run_parity_scan(args, rank, ws, local):
 def run_serve(args, rank, ws, local):
     """Serving: a Poisson stream of simulation requests through qsim_server
     (continuous batching under an HBM budget), FP64 probabilities out.
-    Each distinct M uses one seeded random input state from a page-locked pool."""
+    Each distinct M uses one seeded random input state from a pinned pool."""
     import torch
-    from paper_quant_ph_0308158_gb300 import HostBuffer, Server, build
+    from paper_quant_ph_0308158_gb300 import Server, build
 
     assert torch.cuda.is_available(), "bench.py needs a CUDA device"
     build.build()
     torch.cuda.set_device(local)
     m_hi = args.serve_m_max
     dtype = np.dtype(np.complex128)
-    # Input states: one page-locked block from the library (qsim_host_alloc:
-    # 1 GiB chunks kept where they copy at the link rate; some host ranges of
-    # this machine copy at half the rate or less), sliced per M.
+    # Input states: one pinned block, taken before anything else churns host
+    # memory and sliced per M.  Copies from pinned memory scattered over many
+    # small physical pieces ran at 25-45 GB/s instead of 211 GB/s on the
+    # GB300's host link, so a client should pin large blocks early.
     sizes = {M: 1 << M for M in range(12, m_hi + 1)}
-    block_buf = HostBuffer((sum(sizes.values()) + 256 * len(sizes),), np.complex128)
-    block = torch.from_numpy(block_buf.array)
+    block = torch.empty(sum(sizes.values()) + 256 * len(sizes), dtype=torch.complex128,
+                        pin_memory=True)
     pool, off = {}, 0
     for M in sorted(sizes, reverse=True):
         t = block[off: off + sizes[M]]

@@ -448,16 +448,15 @@ typedef struct qsim_server_stats {
     uint64_t swapped_in;        /* of them brought back to the device           */
 } qsim_server_stats;
 
-/* Reserve hbm_budget_bytes of device memory (one cudaMalloc) and a
- * page-locked host result arena of host_result_bytes (qsim_host_alloc: about a
- * tenth of a second per GiB), create the streams and start the scheduler
- * thread on the current device. */
+/* Reserve hbm_budget_bytes of device memory (one cudaMalloc) and a pinned
+ * host result arena of host_result_bytes, create the streams and start the
+ * scheduler thread on the current device. */
 int qsim_server_create(size_t hbm_budget_bytes, size_t host_result_bytes, int dtype,
                        qsim_server **out);
 
-/* Queue a request.  host_amps (2^M amplitudes of the server's dtype;
- * page-locked memory, best from qsim_host_alloc, uploads fastest) must stay
- * valid and unchanged until the request is done; steps are copied.  QSIM_EINVAL for an invalid circuit, QSIM_EBUSY if
+/* Queue a request.  host_amps (2^M amplitudes of the server's dtype; pinned
+ * memory uploads fastest) must stay valid and unchanged until the request is
+ * done; steps are copied.  QSIM_EINVAL for an invalid circuit, QSIM_EBUSY if
  * the request could never fit the budgets.  *req_id identifies it. */
 int qsim_server_submit(qsim_server *s, uint32_t M, const void *host_amps, const qsim_step *steps,
                        size_t L, uint64_t *req_id);
@@ -619,39 +618,6 @@ int qsim_plan_circuit_ex(uint32_t M, int dtype, const qsim_step *steps, size_t L
  * allocating routine. */
 int qsim_probabilities_noalloc(const void *d_state, uint32_t M, int dtype, double *d_probs,
                                double *d_norm, void *stream);
-
-/* ---- host buffers for the state and the probabilities ---------------------- */
-
-/* Page-locked host memory for transfers to and from the current device (the
- * state in, the probabilities out: App. 1's and Sec. 4's inputs and outputs
- * cross the host link once per circuit).  On a host whose pages do not all
- * reach the link at the same rate (a virtualised Grace host: a few 1 GiB
- * ranges copied at half the rate or less), the request is filled with 1 GiB
- * chunks, each page-locked and timed with one copy in each direction; the
- * chunks within 15 % of the fastest are moved into one contiguous range,
- * which is page-locked as a whole, and the others are freed.
- *   bytes  size of the buffer (> 0); rounded up to whole 1 GiB chunks, or to
- *          2 MiB for requests below 1 GiB (one chunk)
- *   out    receives the base address (2 MiB aligned; 512 MiB for 1 GiB chunks)
- * The memory is uninitialised and owned by the caller until qsim_host_free.
- * It uses the CUDA device current on the calling thread (a 32 MiB device
- * buffer while it measures).  Leaves at least 8 GiB of host memory free:
- * QSIM_ENOMEM when the request (or populating it) would not; QSIM_ECUDA when
- * page-locking fails.  Takes about a tenth of a second per GiB. */
-int qsim_host_alloc(size_t bytes, void **out);
-
-/* Free a buffer of qsim_host_alloc (NULL is a no-op).  QSIM_EINVAL for a
- * pointer that qsim_host_alloc did not return (or already freed). */
-int qsim_host_free(void *p);
-
-/* Device-to-host copies of this context (probabilities to host memory) go on
- * 'stream' (a cudaStream_t owned by the caller, alive until the context is
- * destroyed or another stream is set) instead of the context's private
- * stream; NULL returns to a private one.  Contexts that share one stream
- * queue their copies out in call order, so large copies out of several
- * contexts do not share the link at once.  Waits for the copies already
- * queued on the previous stream. */
-int qsim_set_copy_stream(qsim_ctx *ctx, void *stream);
 
 /* ---- diagnostics ------------------------------------------------------------ */
 

@@ -9,8 +9,8 @@ generators.  Importing the package does not load the library; ``Simulator``
 and ``load()`` do, and raise ``QsimError`` when it is missing.
 """
 from .binding import (QsimError, Simulator, Batch, Server, load, plan_circuit, version,  # noqa: F401
-                      jit_precompile, gather_rows, plan_circuit_ex, HostBuffer, EXPORTS, STRATEGY)
+                      jit_precompile, gather_rows, plan_circuit_ex, EXPORTS, STRATEGY)
 from .workloads import STEP_DTYPE, make_steps  # noqa: F401
 
-__all__ = ["QsimError", "Simulator", "Batch", "Server", "load", "plan_circuit", "version", "jit_precompile", "gather_rows", "plan_circuit_ex", "HostBuffer", "EXPORTS",
+__all__ = ["QsimError", "Simulator", "Batch", "Server", "load", "plan_circuit", "version", "jit_precompile", "gather_rows", "plan_circuit_ex", "EXPORTS",
            "STRATEGY", "STEP_DTYPE", "make_steps"]

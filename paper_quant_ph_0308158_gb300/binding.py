@@ -59,7 +59,6 @@ EXPORTS = (
     "qsim_server_get_stats", "qsim_server_destroy", "qsim_server_drain", "qsim_server_set_backfill",
     "qsim_server_set_paused", "qsim_server_set_tracing", "qsim_server_get_trace",
     "qsim_server_set_copy_streams", "qsim_server_set_upload_chunk", "qsim_server_set_eviction",
-    "qsim_host_alloc", "qsim_host_free", "qsim_set_copy_stream",
 )
 
 
@@ -213,9 +212,6 @@ def load() -> ctypes.CDLL:
             "qsim_server_set_tracing": ([p, i], i),
             "qsim_server_get_trace": ([p, p, sz, ctypes.POINTER(sz)], i),
             "qsim_server_destroy": ([p], None),
-            "qsim_host_alloc": ([sz, pp], i),
-            "qsim_host_free": ([p], i),
-            "qsim_set_copy_stream": ([p, p], i),
             "qsim_last_error": ([], ctypes.c_char_p),
             "qsim_version": ([], ctypes.c_char_p),
         }
@@ -411,11 +407,6 @@ class Simulator:
     def set_coset(self, enable: bool, run_bits: int = 0, stage_kib: int = 0):
         """Affine gathers through coset-blocked tiles (default) or direct reads."""
         _check(self._lib.qsim_set_coset(self._ctx, int(bool(enable)), run_bits, stage_kib))
-
-    def set_copy_stream(self, stream: int = 0):
-        """Queue this context's copies out on a caller's cudaStream_t handle
-        (e.g. ``torch.cuda.Stream().cuda_stream``; 0: a private stream)."""
-        _check(self._lib.qsim_set_copy_stream(self._ctx, ctypes.c_void_p(stream or None)))
 
     def set_wait_test(self, poll_limit: int):
         """Arm the next tile pass to give up its pipeline waits (testing)."""
@@ -714,35 +705,6 @@ def gather_rows(d_in: int, d_out: int, d_rows: int, M: int, dtype, d_probs: int 
     _check(L.qsim_gather_rows(ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), ctypes.c_void_p(d_rows),
                               M, dtype_code(dtype), ctypes.c_void_p(d_probs or None), loads_in_flight,
                               ctypes.c_void_p(stream or None)))
-
-
-class HostBuffer:
-    """Page-locked host memory from qsim_host_alloc (chunks measured for the
-    copy rate they reach, kept where it is full), exposed as a numpy array;
-    freed by close() or when the object is collected."""
-
-    def __init__(self, shape, dtype):
-        self.dtype = np.dtype(dtype)
-        count = int(np.prod(shape))
-        nbytes = max(1, count * self.dtype.itemsize)
-        self._lib = load()
-        ptr = ctypes.c_void_p()
-        _check(self._lib.qsim_host_alloc(nbytes, ctypes.byref(ptr)))
-        self._ptr = ptr.value
-        raw = (ctypes.c_char * nbytes).from_address(self._ptr)
-        self.array = np.frombuffer(raw, dtype=self.dtype, count=count).reshape(shape)
-
-    def close(self):
-        if getattr(self, "_ptr", None):
-            self.array = None
-            _check(self._lib.qsim_host_free(ctypes.c_void_p(self._ptr)))
-            self._ptr = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
 
 
 def version() -> str:

@@ -26,7 +26,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"] + ARCH
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-Wextra", "-Wno-unused-parameter"]
 
-SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "jit.cu", "batch.cu", "server.cu", "hostmem.cu", "planner.cpp"]
+SOURCES = ["kernels.cu", "qsim_api.cu", "noalloc.cu", "jit.cu", "batch.cu", "server.cu", "planner.cpp"]
 HEADERS = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + [
     os.path.join(ROOT, "include", "qsim.h")]
 

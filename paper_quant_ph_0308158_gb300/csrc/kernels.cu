@@ -149,21 +149,62 @@ __device__ __forceinline__ void fence_mbar_init()
 // (a) per-step sweep over toggled pairs
 // ============================================================================
 
-template <int B>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(char *__restrict__ state, SweepParams p)
+// The first index of pair q: a zero inserted at every listed bit (target,
+// controls and, for the paired complex64 form, bit 0), then the polarity.
+__device__ __forceinline__ uint64_t sweep_index(uint64_t q, const SweepParams &p, uint32_t first)
 {
-    using A = typename AmpOf<B>::T;
-    A *st = reinterpret_cast<A *>(state);
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t q = (uint64_t)blockIdx.x * kThreads + threadIdx.x; q < p.n_pairs; q += stride) {
-        uint64_t j = q;
+    uint64_t j = first ? insert_zero(q, 0) : q;
 #pragma unroll 1
-        for (uint32_t s = 0; s < p.nins; ++s) j = insert_zero(j, p.ins[s]);
-        j |= p.pol;
-        const A a = st[j];
-        const A b = st[j + p.half];
-        st[j] = b;
-        st[j + p.half] = a;
+    for (uint32_t s = 0; s < p.nins; ++s) j = insert_zero(j, p.ins[s]);
+    return j | p.pol;
+}
+
+// One step in place, every access 16 bytes wide (uint4), two units per
+// thread in flight.  MODE 0: complex128, a unit is one pair.  complex64 (two
+// amplitudes per vector): MODE 1, target bit 0: a unit is one vector whose
+// halves swap; MODE 2, bit 0 free: a unit is two neighbouring pairs, two
+// whole vectors swap (a high target moves contiguous blocks); MODE 3, bit 0 a
+// control: a unit is one pair, the active half of each of its two vectors
+// swaps and the inactive half is written back unchanged (no other unit of
+// the step touches either vector).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(uint4 *__restrict__ st, SweepParams p, uint64_t units)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    const uint64_t hv = MODE == 0 ? p.half : p.half >> 1;  // partner offset in vectors
+    for (uint64_t q = (uint64_t)blockIdx.x * kThreads + threadIdx.x; q < units; q += 2 * stride) {
+        uint64_t v[2];
+        bool on[2];
+        uint4 a[2], b[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t qq = q + (uint64_t)u * stride;
+            on[u] = qq < units;
+            if (!on[u]) continue;
+            const uint64_t j = sweep_index(qq, p, MODE == 2);
+            v[u] = MODE == 0 ? j : j >> 1;
+            a[u] = st[v[u]];
+            if (MODE != 1) b[u] = st[v[u] + hv];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!on[u]) continue;
+            if (MODE == 1) {
+                st[v[u]] = make_uint4(a[u].z, a[u].w, a[u].x, a[u].y);
+            } else if (MODE == 3) {
+                uint4 x = a[u], y = b[u];
+                if (p.pol & 1ull) {  // the odd halves are the active ones
+                    x.z = b[u].z; x.w = b[u].w; y.z = a[u].z; y.w = a[u].w;
+                } else {
+                    x.x = b[u].x; x.y = b[u].y; y.x = a[u].x; y.y = a[u].y;
+                }
+                st[v[u]] = x;
+                st[v[u] + hv] = y;
+            } else {
+                st[v[u]] = b[u];
+                st[v[u] + hv] = a[u];
+            }
+        }
     }
 }
 
@@ -1328,14 +1369,22 @@ int num_sms()
 int launch_sweep(void *state, int amp_bytes, const SweepParams &p, int * /*d_err*/, void *stream)
 {
     if (p.n_pairs == 0) return cudaSuccess;
-    const uint64_t want = (p.n_pairs + kThreads - 1) / kThreads;
+    // complex64: bit 0 is the target, a control, or free (the lowest
+    // insertion is bit 0 exactly when it is the target or a control)
+    const bool bit0_listed = p.nins > 0 && p.ins[0] == 0;
+    const int mode = amp_bytes == 16 ? 0 : p.half == 1 ? 1 : bit0_listed ? 3 : 2;
+    const uint64_t units = mode == 2 ? p.n_pairs / 2 : p.n_pairs;
+    const uint64_t want = (units + 2 * kThreads - 1) / (2 * kThreads);
     const uint64_t cap = (uint64_t)num_sms() * 8;
-    const int grid = (int)(want < cap ? want : cap);
+    const int grid = (int)(want < cap ? (want ? want : 1) : cap);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (amp_bytes == 8)
-        sweep_kernel<8><<<grid, kThreads, 0, s>>>(static_cast<char *>(state), p);
-    else
-        sweep_kernel<16><<<grid, kThreads, 0, s>>>(static_cast<char *>(state), p);
+    uint4 *st = static_cast<uint4 *>(state);
+    switch (mode) {
+    case 0: sweep_kernel<0><<<grid, kThreads, 0, s>>>(st, p, units); break;
+    case 1: sweep_kernel<1><<<grid, kThreads, 0, s>>>(st, p, units); break;
+    case 2: sweep_kernel<2><<<grid, kThreads, 0, s>>>(st, p, units); break;
+    default: sweep_kernel<3><<<grid, kThreads, 0, s>>>(st, p, units); break;
+    }
     return cudaGetLastError();
 }
 

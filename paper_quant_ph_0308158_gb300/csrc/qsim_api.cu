@@ -71,9 +71,6 @@ struct qsim_ctx {
     cudaEvent_t full_written = nullptr;               // the context's stream wrote it
     bool full_pending = false;
     cudaStream_t copy_stream = nullptr;               // device-to-host copies of those chunks
-    bool own_copy_stream = true;                      // false: the caller's (qsim_set_copy_stream)
-    cudaEvent_t last_copy = nullptr;                  // after the last copy out queued
-    bool copy_pending = false;
     cudaEvent_t chunk_ready[2] = {nullptr, nullptr}, chunk_copied[2] = {nullptr, nullptr};
     PlanOptions opts;
     qsim_plan_stats stats{};
@@ -123,9 +120,7 @@ void ctx_free(qsim_ctx *c)
         if (c->chunk_ready[i]) cudaEventDestroy(c->chunk_ready[i]);
         if (c->chunk_copied[i]) cudaEventDestroy(c->chunk_copied[i]);
     }
-    if (c->copy_pending) cudaEventSynchronize(c->last_copy);  // a shared stream may still copy from here
-    if (c->copy_stream && c->own_copy_stream) cudaStreamDestroy(c->copy_stream);
-    if (c->last_copy) cudaEventDestroy(c->last_copy);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -464,24 +459,8 @@ int qsim_get_plan_stats(qsim_ctx *c, qsim_plan_stats *out)
 int qsim_synchronize(qsim_ctx *c)
 {
     if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
-    if (c->copy_pending) {  // this context's copies only (the copy stream may be shared)
-        QSIM_CUDA(cudaEventSynchronize(c->last_copy), "probability copies");
-        c->copy_pending = false;
-    }
+    if (c->copy_stream) QSIM_CUDA(cudaStreamSynchronize(c->copy_stream), "probability copies");
     return check_device(c);
-}
-
-int qsim_set_copy_stream(qsim_ctx *c, void *stream)
-{
-    if (!c) return fail(QSIM_EINVAL, "ctx is NULL");
-    if (c->copy_pending) {
-        QSIM_CUDA(cudaEventSynchronize(c->last_copy), "probability copies");
-        c->copy_pending = false;
-    }
-    if (c->copy_stream && c->own_copy_stream) QSIM_CUDA(cudaStreamDestroy(c->copy_stream), "cudaStreamDestroy");
-    c->copy_stream = static_cast<cudaStream_t>(stream);
-    c->own_copy_stream = stream == nullptr;
-    return QSIM_OK;
 }
 
 // Record the start of a profiled launch of kernel kind 'kind' with the given
@@ -868,32 +847,13 @@ double *full_probs_buffer(qsim_ctx *c)
     return c->d_probs_full;
 }
 
-// The context's copy stream (its own unless the caller set one), and the
-// event after its latest copy out.
-int ensure_copy_stream(qsim_ctx *c)
-{
-    if (!c->copy_stream) {
-        QSIM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        c->own_copy_stream = true;
-    }
-    if (!c->last_copy)
-        QSIM_CUDA(cudaEventCreateWithFlags(&c->last_copy, cudaEventDisableTiming), "cudaEventCreate");
-    return QSIM_OK;
-}
-
-int note_copies(qsim_ctx *c)
-{
-    QSIM_CUDA(cudaEventRecord(c->last_copy, c->copy_stream), "cudaEventRecord");
-    c->copy_pending = true;
-    return QSIM_OK;
-}
-
 // After the context's stream has written the whole-state buffer: one copy of
 // it to the host on the copy stream.
 int copy_full_probabilities(qsim_ctx *c, double *host_probs)
 {
-    int rc = ensure_copy_stream(c);
-    if (rc != QSIM_OK) return rc;
+    if (!c->copy_stream) {
+        QSIM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    }
     QSIM_CUDA(cudaEventRecord(c->full_written, c->stream), "cudaEventRecord");
     QSIM_CUDA(cudaStreamWaitEvent(c->copy_stream, c->full_written, 0), "cudaStreamWaitEvent");
     QSIM_CUDA(cudaMemcpyAsync(host_probs, c->d_probs_full, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
@@ -901,7 +861,7 @@ int copy_full_probabilities(qsim_ctx *c, double *host_probs)
               "cudaMemcpy(probabilities)");
     QSIM_CUDA(cudaEventRecord(c->full_copied, c->copy_stream), "cudaEventRecord");
     c->full_pending = true;
-    return note_copies(c);
+    return QSIM_OK;
 }
 
 }  // namespace
@@ -946,8 +906,7 @@ int qsim_probabilities(qsim_ctx *c, double *host_probs, size_t n, double *norm_o
     size_t nchunks = 0;
     rc = queue_host_probabilities(c, host_probs, norm_out != nullptr, &nchunks);
     if (rc != QSIM_OK) return rc;
-    QSIM_CUDA(cudaEventSynchronize(c->last_copy), "cudaMemcpy(probabilities)");
-    c->copy_pending = false;
+    QSIM_CUDA(cudaStreamSynchronize(c->copy_stream), "cudaMemcpy(probabilities)");
     rc = check_device(c);
     if (rc != QSIM_OK) return rc;
     if (norm_out) {
@@ -976,9 +935,8 @@ int queue_host_probabilities(qsim_ctx *c, double *host_probs, bool want_norms, s
     // for chunk k+1 runs on the context's stream while chunk k is copied out
     // on a second stream.
     const size_t chunk = c->n < kProbChunk ? c->n : kProbChunk;
-    int rc = ensure_copy_stream(c);
-    if (rc != QSIM_OK) return rc;
-    if (!c->d_probs_chunk[0]) {
+    if (!c->copy_stream) {
+        QSIM_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         for (int i = 0; i < 2; ++i) {
             QSIM_CUDA(cudaMalloc(&c->d_probs_chunk[i], sizeof(double) * chunk), "cudaMalloc(probabilities)");
             QSIM_CUDA(cudaEventCreateWithFlags(&c->chunk_ready[i], cudaEventDisableTiming), "cudaEventCreate");
@@ -1004,7 +962,7 @@ int queue_host_probabilities(qsim_ctx *c, double *host_probs, bool want_norms, s
                   "cudaMemcpy(probabilities)");
         QSIM_CUDA(cudaEventRecord(c->chunk_copied[b], c->copy_stream), "cudaEventRecord");
     }
-    return note_copies(c);
+    return QSIM_OK;
 }
 
 }  // namespace

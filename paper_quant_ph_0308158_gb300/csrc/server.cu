@@ -674,16 +674,12 @@ int qsim_server_create(size_t hbm_budget_bytes, size_t host_result_bytes, int dt
         delete s;
         return sfail(QSIM_ENOMEM, "cudaMalloc(" + std::to_string(hbm_budget_bytes) + " byte HBM budget)");
     }
-    // results (and swapped-out states) leave over the host link: page-locked
-    // chunks kept where they copy at the link rate
-    void *ha = nullptr;
-    if (qsim_host_alloc(host_result_bytes, &ha) != QSIM_OK) {
-        const std::string why = qsim_last_error();
+    e = cudaMallocHost(&s->h_arena, host_result_bytes);
+    if (e != cudaSuccess) {
         cudaFree(s->d_arena);
         delete s;
-        return sfail(QSIM_ENOMEM, "result arena: " + why);
+        return sfail(QSIM_ENOMEM, "cudaMallocHost(result arena)");
     }
-    s->h_arena = static_cast<char *>(ha);
     s->dev.init(hbm_budget_bytes);
     s->host.init(host_result_bytes);
     cudaGetDevice(&s->device);
@@ -920,7 +916,7 @@ void qsim_server_destroy(qsim_server *s)
     cudaFree(s->d_norms);
     if (s->t0_event) cudaEventDestroy(s->t0_event);
     cudaFree(s->d_arena);
-    qsim_host_free(s->h_arena);
+    cudaFreeHost(s->h_arena);
     cudaStreamDestroy(s->compute);
     cudaStreamDestroy(s->h2d);
     cudaStreamDestroy(s->d2h);
