@@ -826,7 +826,7 @@ def run_gather_floor(args, rank, ws, local):
 
     build.build()
     torch.cuda.set_device(local)
-    cfg = workload("mixed_m28")
+    cfg = workload("mixed_m28") if args.floor_m == 28 else W.config_mixed(args.floor_m)
     M, steps = cfg["M"], cfg["steps"]
     n = 1 << M
     stream = torch.cuda.current_stream()
@@ -865,7 +865,7 @@ def run_gather_floor(args, rank, ws, local):
     out["copy_4GiB"] = {"ms": timed(lambda: d_out.copy_(d_in))}
     out["copy_4GiB"]["GBps"] = 2 * 16 * n / out["copy_4GiB"]["ms"] / 1e6
     jit_precompile(M, np.complex128, steps, canonicalize=False)
-    cn = workload("cnot_m28")
+    cn = workload("cnot_m28") if args.floor_m == 28 else W.config_cnot(args.floor_m)
     for name, st, jit, coset in (("jit_gather_mix1000", steps, True, True),
                                  ("coset_gather_cnot1000", cn["steps"], False, True),
                                  ("affine_gather_cnot1000", cn["steps"], False, False)):
@@ -877,7 +877,7 @@ def run_gather_floor(args, rank, ws, local):
             ms = timed(lambda: sim.apply_probabilities(st, probs.data_ptr()))
         out[name] = {"ms": ms, "alg_GBps": alg / ms / 1e6, "frac": alg / ms / 1e6 / peak}
     if rank == 0:
-        print(json.dumps({"workload": "gather_floor_M28_c128", "peak_GBps": peak,
+        print(json.dumps({"workload": "gather_floor_M%d_c128" % M, "peak_GBps": peak,
                           "alg_bytes_per_pass": alg, "results": out}), flush=True)
     return 0
 
@@ -1119,6 +1119,8 @@ def main():
     ap.add_argument("--batch-compare", type=int, default=4096,
                     help="circuits in the default run's batched-vs-plain comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--floor-m", type=int, default=28,
+                    help="gather_floor: state size (the mixed and CNOT circuits at this M)")
     args = ap.parse_args()
     args.also = [w for w in args.also.split(",") if w]
     if args.warmup < 3 and args.impl == "ours":
