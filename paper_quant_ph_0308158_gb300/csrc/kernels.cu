@@ -1,14 +1,17 @@
 // kernels.cu -- sm_103a kernels of the reversible wiring-diagram engine.
 //
-// Every kernel only moves amplitudes (8-byte complex64 or 16-byte
-// complex128 words); index arithmetic is integer.  The one floating-point
-// kernel is the FP64 probability / norm reduction.
+// The circuit kernels only move amplitudes (8-byte complex64 or 16-byte
+// complex128 words); index arithmetic is integer.  Floating point appears in
+// the FP64 probabilities (and their norm) and in the App. 1 product-state
+// input, which is computed, not moved.
 //
 //   sweep_kernel          one step in place over the toggled pairs only
-//                         (Sec. 2b 'intelligent looping').
+//                         (Sec. 2b 'intelligent looping'), 16-byte vectors.
 //   tile_kernel           a run of steps on 2^k-amplitude tiles staged in
 //                         shared memory by bulk-async (TMA) copies, in place
-//                         (Sec. 2i: sequential steps processed together).
+//                         (Sec. 2i: sequential steps processed together);
+//                         optionally generating its sources from the qubits
+//                         of a product state (App. 1).
 //   gather_affine_kernel  k2(i) = k1(A i ^ b) for CNOT/NOT segments
 //                         (Sec. 2h product of the steps, Sec. 2b gather).
 //   gather_coset_kernel   the same map over coset tiles of the output space,
@@ -16,7 +19,15 @@
 //   gather_sliced_kernel  k2(i) = k1(x(i)) with x(i) evaluated for 64 output
 //                         indices at once in bit-sliced form, steps applied
 //                         last to first (Sec. 2h product, Sec. 2b gather).
-//   probs_kernel          p(i) = re^2 + im^2 in FP64 and a norm partial sum.
+//   row_array_kernel      x(i) for every output (the Sec. 2h row array).
+//   gather_rows_kernel    k2(i) = k1(x(i)) from a stored row array.
+//   batch_kernel          one pass level of many circuits (persistent CTAs
+//                         pulling work items).
+//   product_state_kernel  k1(i) = product over qubits of q_b(bit b of i).
+//   probs_kernel          p(i) = re^2 + im^2 in FP64 and a norm partial sum;
+//   probs_pairs_kernel    the same without the norm, two complex64
+//                         amplitudes per 16-byte load.
+// The closed pass and the compiled gather are generated per circuit (jit.cu).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
