@@ -903,6 +903,7 @@ def run_parity_scan(args, rank, ws, local):
         sim = Simulator(M, np.complex64, scratch=False)
         sim.set_strategy("inplace")
         sim.set_canonicalize(False)
+        sim.set_jit(args.jit)  # compiled closed pass (--no-jit: tile pass)
         probs = torch.empty(1 << M, dtype=torch.float64, device="cuda")
         sim.load_product_state(cfg["qubits"])
         for _ in range(args.warmup):
@@ -916,8 +917,14 @@ def run_parity_scan(args, rank, ws, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
+        sim.set_profiling(True)
+        sim.apply_probabilities(steps, probs.data_ptr())
+        sim.synchronize()
+        passes = sim.pass_times()
+        sim.set_profiling(False)
         rows.append({"M": M, "L": len(steps), "ms": ms,
                      "amp_steps_per_s": (1 << M) * len(steps) / (ms * 1e-3),
+                     "kernels": [k for k, _, _ in passes],
                      "gb_per_s": (1 << M) * (8 + 8 + 8) / (ms * 1e-3) / 1e9})
         sim.close()
         del probs
@@ -931,7 +938,7 @@ def run_parity_scan(args, rank, ws, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (the Sec. 4 alternating input from its qubits)",
         "config": {"workload": "parity_scan_M%d_%d" % (lo, hi),
-                   "step_includes": "one in-place tile pass + FP64 probabilities",
+                   "step_includes": "one in-place pass (closed pass, or tile pass with --no-jit) + FP64 probabilities",
                    "per_M": rows,
                    "time_growth_per_qubit": growth,
                    "time_growth_per_qubit_top4_mean": float(np.mean(growth[-4:])) if growth else None,
