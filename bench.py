@@ -602,6 +602,11 @@ def run_ours(args, rank, ws, local):
     batch = None
     if not args.no_batch:
         batch = [batch_speedup(args.batch_compare, mix, 10, 3) for mix in ("cnot", "mixed")]
+
+    # ---- serving (bounded open-loop sample, its own process) -------------------
+    serve = None
+    if rank == 0 and ws == 1 and args.serve_in_line > 0:
+        serve = serve_sample(args)
     if rank == 0:
         stats = r.stats
         line = {
@@ -638,9 +643,40 @@ def run_ours(args, rank, ws, local):
             "clocks": r.clocks,
             "also": also or None,
             "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+def serve_sample(args):
+    """A bounded serving run for the benchmark line: the open-loop Poisson
+    stream of --workload serve with fewer requests and states up to M = 28, in
+    a child process (its page-locked pools and HBM budget come and go with it;
+    this process's cached device memory is released first).  Returns the
+    child's key figures, or a reason it has none."""
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    n = args.serve_in_line
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--serve-requests", str(n),
+           "--serve-rate", "40", "--serve-m-max", "28", "--serve-host-gb", "16",
+           "--serve-plain-requests", str(max(20, n // 12))]
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+    except subprocess.TimeoutExpired:
+        return {"unavailable": "serving sample timed out"}
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    if out.returncode != 0 or not lines:
+        return {"unavailable": "serving sample exited %d: %s" % (out.returncode, out.stderr[-300:])}
+    d = json.loads(lines[-1])
+    c = d["config"]
+    keys = ("requests_per_s", "offered_requests_per_s", "latency_ms_p50", "latency_ms_p99", "wall_s",
+            "h2d_gbs_while_busy", "d2h_gbs_while_busy", "compute_busy_frac", "served_over_plain")
+    r = {"workload": c["workload"] + "_M12-28", "value": d["value"], "unit": d["unit"], "e2e": d["e2e"],
+         "gpu_launches": d["gpu_launches"], "clocks": d["clocks"]}
+    r.update({k: c.get(k) for k in keys})
+    return r
 
 
 def batch_speedup(n: int, mix: str, steps: int, warmup: int):
@@ -1127,6 +1163,8 @@ def main():
     ap.add_argument("--no-coset", action="store_true", help="affine gathers read rows directly")
     ap.add_argument("--coset-run-bits", type=int, default=0, help="coset tile run length r (0: 512 B)")
     ap.add_argument("--coset-stage-kib", type=int, default=0, help="coset pipeline stage (0: 32 KiB)")
+    ap.add_argument("--serve-in-line", type=int, default=1200,
+                    help="requests of the bounded serving sample on the default line (0: none)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison of the default run")
     ap.add_argument("--also", default="mixed_m28,cnot_m28,hybrid_m28,parity_m32",
