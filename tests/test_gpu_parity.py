@@ -769,20 +769,26 @@ def test_product_input_falls_back_when_the_plan_starts_with_a_gather():
     _assert_close_to_product(got, want, np.complex128)
 
 
-def test_sec4_parity_m32_fused_product_input(cuda):
-    """The Sec. 4 example at M = 32 with its input generated inside the one
-    tile pass: every amplitude (-1)^popcount(i) / 2^16 exactly (checked on the
-    device), every probability exactly 2^-32."""
+@pytest.mark.parametrize("jit", [False, True])
+def test_sec4_parity_m32_fused_product_input(cuda, jit):
+    """The Sec. 4 example at M = 32 from its qubits (App. 1): with compiled
+    kernels off, the input is generated inside the one tile pass; with them on
+    (as benchmarked: AUTO with a scratch buffer), the planner writes the input
+    with the product-state kernel and runs one closed pass.  Every amplitude
+    (-1)^popcount(i) / 2^16 exactly (checked on the device), every
+    probability exactly 2^-32."""
     torch = cuda
     M = 32
     cfg = W.config_parity(M)
     probs = torch.empty(1 << M, dtype=torch.float64, device="cuda")
-    with Simulator(M, np.complex64, scratch=False) as sim:
-        sim.set_strategy("inplace")
+    with Simulator(M, np.complex64, scratch=jit) as sim:
+        sim.set_strategy("auto" if jit else "inplace")
+        sim.set_jit(jit)
+        sim.set_canonicalize(False)
         sim.set_profiling(True)
         sim.apply_product(cfg["qubits"], cfg["steps"], probs.data_ptr())
         sim.synchronize()
-        assert [k for k, _, _ in sim.pass_times()] == ["tile_kernel"]
+        assert [k for k, _, _ in sim.pass_times()] == (["qsim_jit_closed"] if jit else ["tile_kernel"])
         st = sim.state_tensor().view(torch.float32).view(-1, 2)
         assert bool((st[:, 1] == 0).all())
         re = st[:, 0]
