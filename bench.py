@@ -651,16 +651,18 @@ def run_ours(args, rank, ws, local):
 
 def serve_sample(args):
     """A bounded serving run for the benchmark line: the open-loop Poisson
-    stream of --workload serve with fewer requests and states up to M = 28, in
-    a child process (its page-locked pools and HBM budget come and go with it;
-    this process's cached device memory is released first).  Returns the
+    stream of --workload serve at its 200 requests/s (over capacity, so the
+    rate served is the server's capacity and compares with one request at a
+    time through the plain API) with fewer requests and states up to M = 28,
+    in a child process (its page-locked pools and HBM budget come and go with
+    it; this process's cached device memory is released first).  Returns the
     child's key figures, or a reason it has none."""
     import torch
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     n = args.serve_in_line
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--serve-requests", str(n),
-           "--serve-rate", "40", "--serve-m-max", "28", "--serve-host-gb", "16",
+           "--serve-rate", "200", "--serve-m-max", "28", "--serve-host-gb", "16",
            "--serve-plain-requests", str(max(20, n // 12))]
     try:
         out = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
