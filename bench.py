@@ -470,6 +470,11 @@ def measure_e2e(args, cfg, r, local, ws, steps_k):
     M, dtype, steps = cfg["M"], np.dtype(cfg["dtype"]), cfg["steps"]
     n = 1 << M
     L = len(steps)
+    need = n * dtype.itemsize + 2 * n * 8 + (8 << 30)  # input, two outputs, headroom
+    budget = getattr(args, "host_budget", 0)
+    if budget and need > budget:
+        return {"unavailable": "host memory: the end-to-end leg page-locks %.0f GiB per rank, "
+                               "this rank's share of the node is %.0f GiB" % (need / 2**30, budget / 2**30)}
     outs_block = torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
     stream = torch.cuda.current_stream()
     s2 = torch.cuda.Stream()
@@ -549,6 +554,9 @@ def run_ours(args, rank, ws, local):
     from paper_quant_ph_0308158_gb300 import build
 
     assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    # host memory this rank may page-lock: the ranks of one node share it
+    free0 = _host_free_bytes()
+    args.host_budget = free0 // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", "1"))) if free0 else 0
     build.build()
     torch.cuda.set_device(local)
     cfg = workload(args.workload)
