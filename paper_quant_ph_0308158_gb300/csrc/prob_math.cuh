@@ -21,8 +21,9 @@
 // in integer arithmetic as well -- align, guard and sticky bits, round to
 // nearest-even -- was measured slower: about 80 integer instructions cost
 // more issue slots than one FP64 add.)  Normal numbers and zeros take a
-// short inlined path (the significand square is normalised by a shift of
-// (P << 6) >> (P >> 47)); the rest an out-of-line general one.
+// short inlined path in 32-bit halves (P = hi:lo from a multiply and its high
+// half; P shifted left by 6 - (P >> 47) puts its leading bit on bit 52, where
+// it adds one to the exponent field); the rest an out-of-line general one.
 //
 // complex128: im^2 rounded, then one fused multiply-add -- within one unit in
 // the last place of two separately rounded products.
@@ -31,13 +32,14 @@
 #define QSIM_PROB_MATH(Q, QN)                                                               \
     Q unsigned long long qsim_square_bits_fast(unsigned int u)                              \
     {                                                                                       \
-        const unsigned int e = (u >> 23) & 0xFFu;                                           \
         const unsigned int s = (u & 0x7FFFFFu) | 0x800000u;                                 \
-        const unsigned long long P = (unsigned long long)s * s;                             \
-        const unsigned int top = (unsigned int)(P >> 47);                                   \
-        const unsigned long long S = (P << 6) >> top;                                       \
-        const unsigned long long bits = ((unsigned long long)(2u * e + 768u + top) << 52) + S; \
-        return (u << 1) ? bits : 0ull;                                                      \
+        const unsigned int lo = s * s, hi = __umulhi(s, s);                                 \
+        const unsigned int top = hi >> 15;                                                  \
+        const unsigned int sh = 6u - top;                                                   \
+        const unsigned int shi = __funnelshift_l(lo, hi, sh);                               \
+        const unsigned int ex = ((u >> 23) & 0xFFu) * 2u + 768u + top;                      \
+        const unsigned int bhi = (ex << 20) + shi;                                          \
+        return (u << 1) ? (((unsigned long long)bhi << 32) | (lo << sh)) : 0ull;            \
     }                                                                                       \
     QN unsigned long long qsim_square_bits(unsigned int u)                                  \
     {                                                                                       \

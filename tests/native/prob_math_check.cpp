@@ -19,6 +19,15 @@ static inline double __dadd_rn(double a, double b) { return a + b; }
 static inline double __dmul_rn(double a, double b) { return a * b; }
 static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 static inline int __clzll(long long v) { return v ? __builtin_clzll((unsigned long long)v) : 64; }
+static inline unsigned int __umulhi(unsigned int a, unsigned int b)
+{
+    return (unsigned int)(((unsigned long long)a * b) >> 32);
+}
+static inline unsigned int __funnelshift_l(unsigned int lo, unsigned int hi, unsigned int shift)
+{
+    const unsigned int s = shift & 31u;  // CUDA's wrapping form
+    return s ? (hi << s) | (lo >> (32u - s)) : hi;
+}
 static inline double __hiloint2double(int hi, int lo)
 {
     const unsigned long long b = ((unsigned long long)(unsigned int)hi << 32) | (unsigned int)lo;
