@@ -125,12 +125,14 @@ int qsim_load_state(qsim_ctx *ctx, const void *host_amps, size_t n_amps);
 /* Set the state to the product state of App. 1 without sending 2^M
  * amplitudes: k1(i) = product over bits b of q_b(bit b of i), where qubits
  * holds 4*M doubles (re q_b(0), im q_b(0), re q_b(1), im q_b(1)) for b = 0
- * (the paper's a(1)) to M-1.  Computed on the device in FP64 as the product
- * of the factors of the bits above the lowest min(M, 10) times the product
- * of the factors of those lowest bits, each partial product taken from the
- * most significant bit down, every real product and sum rounded separately;
- * complex64 states are rounded once at the end.  Queued on the context's
- * stream; qubits is copied during the call. */
+ * (the paper's a(1)) to M-1.  Computed on the device as the product of the
+ * factors of the bits above the lowest min(M, 10) (three partial products of
+ * up to 8 bits each) times the product of the factors of those lowest bits;
+ * every partial product is taken in FP64 from the most significant bit down,
+ * every real product and sum rounded separately.  complex128 multiplies the
+ * partial products in FP64; complex64 in float-float arithmetic (about 48
+ * significant bits, within 2^-42 of |k1(i)|) and rounds once at the end.
+ * Queued on the context's stream; qubits is copied during the call. */
 int qsim_load_product_state(qsim_ctx *ctx, const double *qubits);
 
 /* Apply a circuit to the product state of App. 1 (qubits as for
@@ -141,7 +143,10 @@ int qsim_load_product_state(qsim_ctx *ctx, const double *qubits);
  * over its low bits once per pass, all in FP64; for complex64 the per-output
  * product of the last two is taken in float-float arithmetic (about 48
  * significant bits) and rounded once, for complex128 in FP64.  Other plans
- * start from qsim_load_product_state.  The context's state is overwritten.
+ * start from qsim_load_product_state.  With compiled kernels on, the planner
+ * also weighs a plan without closed passes (a closed pass cannot generate the
+ * input) and keeps the one estimated cheaper with the input's cost included.
+ * The context's state is overwritten.
  * d_probs NULL: no probabilities; else as qsim_apply_circuit_probabilities.
  * Errors as qsim_apply_circuit. */
 int qsim_apply_circuit_product(qsim_ctx *ctx, const double *qubits, const qsim_step *steps, size_t L,
