@@ -120,3 +120,44 @@ def test_auto_is_never_estimated_slower_than_a_pure_plan():
             for s in ("inplace", "gather"):
                 other = _plan(M, dtype, steps, strategy=s, jit=bool(seed & 1))
                 assert auto["stats"]["est_ms"] <= other["stats"]["est_ms"] * (1 + 1e-12)
+
+
+def _changed_bits(M, steps, rows=1 << 16, seed=5):
+    """The bits a circuit's row map changes, from sampled rows of the oracle's
+    single-row evaluation (enough rows to see every changed bit here)."""
+    import oracle
+    r = np.random.default_rng(seed).integers(0, 1 << M, size=rows, dtype=np.uint64)
+    return int(np.bitwise_or.reduce(oracle.source_rows(M, steps, r).astype(np.uint64) ^ r))
+
+
+def test_adder_m32_in_place_is_one_closed_pass():
+    """With compiled kernels and the circuit's changed-bit set known, the
+    M = 32 adder in place is one closed pass, estimated near its measured
+    11.8 ms (without probabilities); without compiled kernels it needs
+    dozens of tile passes."""
+    cfg = W.config_adder_m32()
+    delta = _changed_bits(32, cfg["steps"])
+    assert bin(delta).count("1") == 12
+    r = _plan(cfg, strategy="inplace", scratch=False, jit=True, closed_delta=delta)
+    assert r["variants"] == ["closed"]
+    assert 10.0 < r["stats"]["est_ms"] < 14.0
+    t = _plan(cfg, strategy="inplace", scratch=False, jit=False)
+    assert set(t["variants"]) <= {"tile", "sweep"} and len(t["variants"]) > 30
+
+
+@pytest.mark.parametrize("dtype,kmax", [(np.complex64, 14), (np.complex128, 13)])
+def test_closed_pass_needs_the_changed_bits_to_fit_a_tile(dtype, kmax):
+    """One closed pass covers a whole circuit only while the bits it changes
+    fit one tile (14 bits of complex64, 13 of complex128): a circuit whose
+    targets fill the low kmax bits is one pass, one whose targets fill kmax + 1
+    bits needs more."""
+    M = 24
+    for width, one_pass in ((kmax, True), (kmax + 1, False)):
+        steps = W.local_mixed_circuit(M, 300, 3, width)
+        delta = _changed_bits(M, steps)
+        assert delta == (1 << width) - 1
+        r = _plan(M, dtype, steps, strategy="inplace", scratch=False, jit=True, closed_delta=delta)
+        if one_pass:
+            assert r["variants"] == ["closed"]
+        else:
+            assert len(r["variants"]) >= 2
