@@ -303,66 +303,10 @@ __device__ __forceinline__ void consumer_sync()
 // producer finds the CTA's next tile with an active step, publishes its
 // base and active-step mask in the stage's metadata, and issues one bulk
 // copy per contiguous run of 2^l amplitudes; an empty tile marks the end.
-// Float-float complex number (each part an unevaluated sum hi + lo of two
-// floats, about 48 significant bits): the product-input pass multiplies in it
-// so that complex64 amplitudes cost FP32 work, not FP64 issue.
-struct FFc {
-    float rh, rl, ih, il;
-};
-
-__device__ __forceinline__ FFc ffc_of(double2 v)
-{
-    FFc r;
-    r.rh = __double2float_rn(v.x);
-    r.rl = __double2float_rn(v.x - (double)r.rh);
-    r.ih = __double2float_rn(v.y);
-    r.il = __double2float_rn(v.y - (double)r.ih);
-    return r;
-}
-
-// x*y + sign*z*w in float-float (error-free products by fma, Dekker/Knuth
-// two-sum for the high parts), rounded to one float at the end.
-__device__ __forceinline__ float ff_dot2_round(float xh, float xl, float yh, float yl, float zh, float zl,
-                                               float wh, float wl, float sign)
-{
-    const float p1 = xh * yh;
-    const float e1 = fmaf(xh, yh, -p1);
-    const float p2 = sign * zh * wh;
-    const float e2 = fmaf(sign * zh, wh, -p2);
-    const float s = p1 + p2;  // two-sum of the high products
-    const float bb = s - p1;
-    const float err = (p1 - (s - bb)) + (p2 - bb);
-    const float cross = fmaf(xh, yl, xl * yh) + sign * fmaf(zh, wl, zl * wh);
-    return s + (err + e1 + e2 + cross);
-}
-
-// x*y + sign*z*w kept in float-float (hi, lo).
-__device__ __forceinline__ float2 ff_dot2(float xh, float xl, float yh, float yl, float zh, float zl, float wh,
-                                          float wl, float sign)
-{
-    const float p1 = xh * yh;
-    const float e1 = fmaf(xh, yh, -p1);
-    const float p2 = sign * zh * wh;
-    const float e2 = fmaf(sign * zh, wh, -p2);
-    const float s = p1 + p2;
-    const float bb = s - p1;
-    const float err = (p1 - (s - bb)) + (p2 - bb);
-    const float lo = err + e1 + e2 + fmaf(xh, yl, xl * yh) + sign * fmaf(zh, wl, zl * wh);
-    const float h = s + lo;
-    return make_float2(h, lo - (h - s));
-}
-
-__device__ __forceinline__ FFc ffc_mul(const FFc &a, const FFc &b)
-{
-    const float2 re = ff_dot2(a.rh, a.rl, b.rh, b.rl, a.ih, a.il, b.ih, b.il, -1.0f);
-    const float2 im = ff_dot2(a.rh, a.rl, b.ih, b.il, a.ih, a.il, b.rh, b.rl, 1.0f);
-    FFc r;
-    r.rh = re.x;
-    r.rl = re.y;
-    r.ih = im.x;
-    r.il = im.y;
-    return r;
-}
+// Float-float complex products of the product-input pass (FP32 work, not
+// FP64 issue), written so that no multiply-add contraction can break their
+// error-free parts.
+#include "ff_math.cuh"
 
 __device__ __forceinline__ double2 dcmul(double2 a, double2 b)
 {

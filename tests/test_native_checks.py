@@ -11,6 +11,8 @@ the C ABI.
 - arena_check: the serving budget's first-fit allocator (coverage, no
   overlap, merged free blocks, counters);
 - prob_math_check: the complex64 probability arithmetic against the FPU;
+- ff_math_check: the float-float products of the App. 1 input against long
+  double products;
 - closed_source_dump: the generated closed tile pass, evaluated on the host
   and compiled with NVRTC."""
 import os
@@ -46,6 +48,19 @@ def test_probability_arithmetic_matches_the_fpu(tmp_path):
     exe = tmp_path / "prob_math_check"
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe),
                     os.path.join(ROOT, "tests", "native", "prob_math_check.cpp")], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("ok:"), r.stdout + r.stderr
+
+
+def test_float_float_products_within_their_bounds(tmp_path):
+    """The float-float complex arithmetic of the App. 1 input (ff_math.cuh
+    compiled for the host, every operation one correctly rounded step): FP64
+    splits within 2^-48, single products within 2^-43 of |a||b|, the device's
+    two product chains within 2^-41 of |k| and rounding to within one float
+    ulp of the exact product, on six million cases."""
+    exe = tmp_path / "ff_math_check"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-o", str(exe),
+                    os.path.join(ROOT, "tests", "native", "ff_math_check.cpp")], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok:"), r.stdout + r.stderr
 
