@@ -84,3 +84,22 @@ def test_reference_arm_without_room_for_the_fp64_state(monkeypatch, capsys):
     d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert d["impl"] == "reference" and d["value"] > 0
     assert "single-row evaluation" in d["cpu_baseline"]["sample"]
+
+
+def test_profile_summaries_name_their_commands():
+    """Each ncu summary under profiles/ gives the command that made it, and
+    every ncu command there leaves the GPU clocks alone."""
+    d = os.path.join(ROOT, "profiles")
+    mds = [f for f in os.listdir(d) if f.endswith(".md")]
+    assert mds
+    for f in mds:
+        text = open(os.path.join(d, f)).read()
+        lines = text.splitlines()
+        starts = [i for i, l in enumerate(lines) if l.strip().startswith("ncu ")]
+        assert starts, f
+        for i in starts:
+            cmd = lines[i]
+            while cmd.rstrip().endswith("\\") and i + 1 < len(lines):
+                i += 1
+                cmd += lines[i]
+            assert "--clock-control none" in cmd, (f, cmd)
